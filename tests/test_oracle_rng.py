@@ -1,0 +1,141 @@
+"""Pins for the oracle's pair noise xi_ij (Sec. 2.1: symmetric, zero mean,
+unit variance, uncorrelated across pairs and steps).
+
+The generator behind it is Philox-4x32-R (Salmon et al., SC'11).  Published
+known-answer vectors are not available here, so the block function is pinned
+against an independent library implementation of the same published
+algorithm: Triton's ``tl.philox`` run on the CPU by Triton's interpreter.
+"""
+
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+_TRITON_SCRIPT = textwrap.dedent(r"""
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import numpy as np, torch, triton, triton.language as tl
+
+    @triton.jit
+    def kern(c0, c1, c2, c3, o0, o1, o2, o3, seed, ROUNDS: tl.constexpr, N: tl.constexpr):
+        i = tl.arange(0, N)
+        r0, r1, r2, r3 = tl.philox(seed, tl.load(c0 + i), tl.load(c1 + i), tl.load(c2 + i),
+                                   tl.load(c3 + i), ROUNDS)
+        tl.store(o0 + i, r0); tl.store(o1 + i, r1); tl.store(o2 + i, r2); tl.store(o3 + i, r3)
+
+    cfg = json.loads(sys.argv[1])
+    out = []
+    for case in cfg:
+        ctr = np.array(case["ctr"], dtype=np.uint32).reshape(4, -1)
+        n = ctr.shape[1]
+        c = [torch.from_numpy(ctr[k].view(np.int32).copy()) for k in range(4)]
+        o = [torch.zeros(n, dtype=torch.int32) for _ in range(4)]
+        kern[(1,)](*c, *o, case["seed"], ROUNDS=case["rounds"], N=n)
+        out.append([t.numpy().view(np.uint32).tolist() for t in o])
+    print(json.dumps(out))
+""")
+
+
+def _triton_philox(cases):
+    import json
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT, json.dumps(cases)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {r.stderr.strip().splitlines()[-1:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_philox_block_matches_independent_implementation():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(11)
+    cases = []
+    for rounds in (10, 7):
+        for _ in range(3):
+            n = 64
+            ctr = rng.integers(0, 2**32, size=(4, n), dtype=np.uint64).astype(np.uint32)
+            ctr[:, 0] = 0                        # all-zero counter
+            ctr[:, 1] = 0xFFFFFFFF               # all-ones counter
+            seed = int(rng.integers(0, 2**63))
+            cases.append({"ctr": ctr.ravel().tolist(), "seed": seed, "rounds": rounds})
+    cases.append({"ctr": [0] * 64, "seed": 0, "rounds": 10})
+    ref = _triton_philox(cases)
+    for case, want in zip(cases, ref):
+        ctr = np.array(case["ctr"], dtype=np.uint32).reshape(4, -1)
+        key = [case["seed"] & 0xFFFFFFFF, case["seed"] >> 32]
+        for k in range(ctr.shape[1]):
+            got = O.philox4x32(ctr[:, k], key, case["rounds"])
+            assert list(got) == [want[w][k] for w in range(4)], (case["rounds"], k)
+
+
+def test_pair_word_uses_documented_counter_and_key():
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(12)
+    n = 64
+    ida = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    idb = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    step = (1 << 33) + 12345
+    seed = 0x0123456789ABCDEF
+    words, _ = O.pair_rng(ida, idb, step, seed)
+    lo = np.minimum(ida, idb)
+    hi = np.maximum(ida, idb)
+    ctr = np.stack([lo, hi, np.full(n, step & 0xFFFFFFFF, np.uint32),
+                    np.full(n, step >> 32, np.uint32)]).astype(np.uint32)
+    ref = _triton_philox([{"ctr": ctr.ravel().tolist(), "seed": seed, "rounds": 10}])[0]
+    assert words.tolist() == ref[0]
+
+
+def test_xi_is_symmetric_in_the_pair():
+    rng = np.random.default_rng(1)
+    a = rng.integers(0, 2**32, 10000, dtype=np.uint64).astype(np.uint32)
+    b = rng.integers(0, 2**32, 10000, dtype=np.uint64).astype(np.uint32)
+    w_ab, x_ab = O.pair_rng(a, b, 77, 5)
+    w_ba, x_ba = O.pair_rng(b, a, 77, 5)
+    assert np.array_equal(w_ab, w_ba)
+    assert np.array_equal(x_ab, x_ba)
+
+
+def test_xi_map_extremes():
+    s3 = math.sqrt(3.0)
+    assert O.xi_from_word(0) == pytest.approx(s3 * (2.0 ** -24 - 1.0), abs=1e-15)
+    assert O.xi_from_word(0xFFFFFFFF) == pytest.approx(s3 * (1.0 - 2.0 ** -24), abs=1e-15)
+    assert O.xi_from_word(0x80000000) == pytest.approx(s3 * 2.0 ** -24, abs=1e-18)
+    # the low 8 bits do not enter
+    assert O.xi_from_word(0x12345600) == O.xi_from_word(0x123456FF)
+
+
+def test_xi_statistics_zero_mean_unit_variance_uniform():
+    n = 4_000_000
+    ida = np.arange(n, dtype=np.uint32)
+    idb = ida + np.uint32(1)
+    _, xi = O.pair_rng(ida, idb, step=3, seed=2024)
+    m, var = xi.mean(), xi.var()
+    assert abs(m) < 5.0 / math.sqrt(n)
+    # var of the sample variance of a unit-variance uniform: (mu4 - 1)/n, mu4 = 9/5
+    assert abs(var - 1.0) < 5.0 * math.sqrt(0.8 / n)
+    assert xi.min() > -math.sqrt(3.0) and xi.max() < math.sqrt(3.0)
+    hist, _ = np.histogram(xi, bins=64, range=(-math.sqrt(3), math.sqrt(3)))
+    exp = n / 64
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    assert chi2 < 63 + 6 * math.sqrt(2 * 63)
+
+
+def test_xi_uncorrelated_across_steps_and_pairs():
+    n = 1_000_000
+    rng = np.random.default_rng(3)
+    ida = rng.integers(0, 2**20, n, dtype=np.uint64).astype(np.uint32)
+    idb = ida + rng.integers(1, 64, n, dtype=np.uint64).astype(np.uint32)
+    _, x0 = O.pair_rng(ida, idb, 100, 9)
+    _, x1 = O.pair_rng(ida, idb, 101, 9)          # next step, same pairs
+    _, x2 = O.pair_rng(ida, idb + np.uint32(1), 100, 9)   # neighbouring pair
+    _, x3 = O.pair_rng(ida, idb, 100, 10)         # another seed
+    tol = 5.0 / math.sqrt(n)
+    for other in (x1, x2, x3):
+        assert abs(np.mean(x0 * other)) < tol
