@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""DPD fluid-step benchmark on GB300: particle-steps/s.
+
+Workload (default): one periodic box L = 128 rc, rho = 3 (6,291,456
+particles), a = 25, gamma = 4.5, kT = 1, dt = 0.005, seeded uniform positions
+and Maxwellian velocities.  A step is the whole hot path: kick/drift/wrap and
+cell count, scan, stable reorder, pair forces with the Philox pair noise.
+
+  value     particle-steps/s with the state resident in HBM (CUDA events on the
+            library's stream around K steps, max over ranks)
+  e2e       the same metric through the C ABI with host buffers: upload from
+            pinned memory, K steps each followed by a statistics read-back,
+            download of the final state
+  roofline  the force kernel against the FP32/INT32 issue peak
+            (SMs x 128 lanes x SM clock), timed with per-stage events
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+
+`--impl reference` times the oracle alone (the reference arm of this build).
+With --gpus N > 1 (torchrun) every rank steps its own independent replica.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DPD particle-steps/s on 1 GB300, batched vs one-box-at-a-time; p50/p99 latency"
+UNIT = "particle-steps/s"
+
+# Algorithmic ALU issue slots of the force stage per particle-step, with each
+# candidate and each interacting pair counted once (what Newton's third law
+# leaves to do): a candidate test is 7 lane instructions (3 subtractions, a
+# multiply and two fused multiply-adds for r^2, one compare); an interacting
+# pair is 85 (about 25 FP32 instructions for r, w, e . v_ij and the force
+# update, and 60 integer instructions for Philox-4x32-10 and the noise map).
+CAND_SLOTS = 7
+PAIR_SLOTS = 85
+
+
+def force_slots_per_particle(rho: float) -> float:
+    cands = 27.0 * rho / 2.0                 # 27-cell stencil, each pair once
+    pairs = (4.0 * math.pi / 3.0) * rho / 2.0
+    return cands * CAND_SLOTS + pairs * PAIR_SLOTS
+
+
+# Algorithmic HBM bytes per particle-step of the streaming stages.
+STAGE_BYTES = {
+    "integrate_bin": 48 + 32 + 8,            # read x, v, f; write x', v', cell, arrival rank
+    "bin_keys": 8 + 4,                       # read cell, rank; write key
+    "bin_scatter": 8 + 32 + 32,              # read cell, x', v'; write x, v
+}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(L: float, rho: float, steps: int, seed: int = 0) -> dict:
+    """The FP64 oracle (cell-list mode, OpenMP over the host cores) on a
+    bounded sample: a box of the same recipe, `steps` steps after the initial force."""
+    import oracle as O
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+    x, v = uniform_box_state(L, rho=rho, seed=seed)
+    p = O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=seed)
+    st = O.State(p, x, v, mode=O.MODE_CELLS)
+    t0 = time.perf_counter()
+    st.run(steps)
+    dt = time.perf_counter() - t0
+    return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"L={L:g} box of the same recipe ({x.shape[0]} particles, rho={rho:g}), "
+                      f"{steps} step(s) after the initial force, FP64 cell-list mode"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    L_sample = args.ref_L
+    base = cpu_baseline(L_sample, args.rho, 1)   # warm the library and page in
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        cpu_baseline(L_sample, args.rho, 1, seed=1)
+    t_steps = time.perf_counter()
+    for k in range(args.steps):
+        vals.append(cpu_baseline(L_sample, args.rho, 1, seed=2 + k)["value"])
+    elapsed = time.perf_counter() - t_steps
+    value = statistics.mean(vals)
+    n = base["sample"]
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * elapsed / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"dpd_periodic_box_L{args.L:g}_rho{args.rho:g}",
+                   "reference_sample_L": L_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                         "sample": n},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1911_04712_gb300 import build as _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist:
+        dist.barrier()
+    import paper_1911_04712_gb300.dpd as dpd
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+
+    L, rho = args.L, args.rho
+    x, v = uniform_box_state(L, rho=rho, seed=args.seed + rank)
+    n = x.shape[0]
+    stream = torch.cuda.current_stream()
+    box = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed + rank,
+                  stencil=(1 if args.stencil == "half" else 0), stream=stream)
+    box.set_state(x, v)
+    box.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    clocks = ClockSampler(local).start() if not args.no_clocks else None
+    # ---- device-resident timed region
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * args.steps * world / (ms / 1000.0)
+
+    # ---- per-stage events (same workload, same stream) for the roofline
+    stage_ms = box.profile(args.steps)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+    clock_src = "median SM clock sampled during the timed region"
+    if not (clk or {}).get("sm_mhz"):
+        clock_src = "median SM clock under load from MEASURED_PEAKS.json"
+    alu_peak = sms * 128 * float(sm_mhz) * 1e6 / 1e12 if sm_mhz else None   # T lane-ops/s
+    force_ms = stage_ms[4]
+    slots = force_slots_per_particle(rho) * n
+    achieved = slots / (force_ms / 1000.0) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    stages = {}
+    for name, t in zip(dpd.STAGE_NAMES, stage_ms):
+        d = {"ms": round(t, 5), "share": round(t / sum(stage_ms), 4)}
+        if name in STAGE_BYTES:
+            gbs = STAGE_BYTES[name] * n / (t / 1000.0) / 1e9
+            d.update({"GB/s": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3)})
+        stages[name] = d
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+        hv = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+        hp.numpy()[:] = x
+        hv.numpy()[:] = v
+        ebox = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed + rank,
+                       stencil=(1 if args.stencil == "half" else 0), stream=stream)
+        ebox.set_state(hp.numpy(), hv.numpy())      # warm allocation
+        ebox.step(2)
+        ebox.stats()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ebox.set_state(hp.numpy(), hv.numpy())
+        for _ in range(args.steps):
+            ebox.step(1)
+            ebox.stats()
+        ebox.get_state_into(hp.numpy(), hv.numpy())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": n * args.steps * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(round(24 * n / args.steps)),
+               "d2h_bytes_per_step": int(round(24 * n / args.steps)) + 64,
+               "what": "set_state from pinned host, K x (step + FP64 stats read-back), "
+                       "get_state to pinned host"}
+        ebox.close()
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(args.cpu_L, rho, args.cpu_steps)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"dpd_periodic_box_L{L:g}_rho{rho:g}", "particles": n,
+                       "L": L, "rho": rho, "a": 25.0, "gamma": 4.5, "kT": 1.0, "dt": 0.005,
+                       "stencil": args.stencil, "l2": "state larger than L2 "
+                       f"({48 * n / 1e6:.0f} MB of float4 x, v, f)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "kernel": "force", "achieved": achieved,
+                         "peak": alu_peak, "unit": "T lane-ops/s",
+                         "frac": (achieved / alu_peak) if alu_peak else None, "traffic": None,
+                         "peak_from": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_mhz} MHz "
+                                      f"({clock_src})"},
+            "stages": stages,
+            "gpu_launches": dpd.KERNELS_PER_STEP * args.steps,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": base,
+        }
+        print(json.dumps(out), flush=True)
+    box.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--L", type=float, default=128.0)
+    ap.add_argument("--rho", type=float, default=3.0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--stencil", choices=("full", "half"), default="full")
+    ap.add_argument("--cpu-L", type=float, default=64.0)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--ref-L", type=float, default=32.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * dpd.h -- C ABI of the GB300 DPD fluid-step library (libdpd.so).
+ *
+ * The library advances a dissipative particle dynamics (DPD) fluid in
+ * periodic boxes, following the method of the MiRheo paper:
+ *   - Newton's equations of motion (Sec. 2.1, Eq. 1) with m the particle mass;
+ *   - pair forces F_i = sum_j (F^C_ij + F^D_ij + F^R_ij) (Eq. 2):
+ *       F^C = a w(r) e_ij,  w(r) = 1 - r/rc for r < rc, else 0  (Eqs. 3-4),
+ *       F^D = -gamma w_D(r) (v_ij . e_ij) e_ij,
+ *       F^R = sigma w_R(r) xi_ij e_ij / sqrt(dt)                  (Eq. 5),
+ *     with sigma^2 = 2 gamma kT, w_D = w_R^2, w_R = w^k (Sec. 2.1);
+ *   - the noise xi_ij is stateless and pair-symmetric: word 0 of
+ *     Philox-4x32-10 on the counter (min id, max id, step lo, step hi) with key
+ *     (seed lo, seed hi), mapped to xi = sqrt(3)(2U - 1),
+ *     U = ((u >> 8) + 1/2) 2^-24 (zero mean, unit variance);
+ *   - cell lists rebuilt every step (Sec. 3.2): counting sort of particles
+ *     into cells of edge h_d = L_d / floor(L_d / rc) >= rc, exclusive scan,
+ *     stable reorder; forces summed over the 27 neighbouring cells;
+ *   - velocity-Verlet with the velocity predicted at the half step (the fused
+ *     leapfrog of Sec. 3.1, item 5): v += dt/2 F/m; x += dt v (wrapped into
+ *     [0, L)); F = F(x, v); v += dt/2 F/m.
+ *
+ * Step index of the noise: the force computed by dpd_set_state uses step 0;
+ * the force computed during the k-th call-counted step uses step k.
+ *
+ * Arithmetic: FP32 state and forces; FP64 for box-level reductions.
+ *
+ * Conventions for every call:
+ *   - returns DPD_OK (0) or a negative DPD_ERR_* status; never aborts or
+ *     exits; on failure dpd_last_error() gives a message (thread-local);
+ *   - "where" arguments say whether a pointer is host memory
+ *     (DPD_WHERE_HOST) or device memory of the current CUDA device
+ *     (DPD_WHERE_DEVICE); the caller owns every buffer it passes and the
+ *     library copies what it needs before returning;
+ *   - arrays of 3-vectors are n x 3, row-major (x0 y0 z0 x1 y1 z1 ...);
+ *   - a context lives on the CUDA device that was current at creation and
+ *     enqueues all work on its stream (default: the legacy default stream);
+ *     calls on one context are not thread-safe.
+ */
+#ifndef DPD_H
+#define DPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DPD_API __attribute__((visibility("default")))
+#else
+#define DPD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define DPD_OK 0
+#define DPD_ERR_ARG (-1)      /* invalid argument                                  */
+#define DPD_ERR_NOMEM (-2)    /* device or host allocation failed / budget exceeded */
+#define DPD_ERR_CUDA (-3)     /* a CUDA runtime call failed                         */
+#define DPD_ERR_STATE (-4)    /* call out of order (e.g. step before set_state)     */
+#define DPD_ERR_NUMERIC (-5)  /* device flagged a non-finite position or force      */
+#define DPD_ERR_TIMEOUT (-6)  /* a bounded wait expired                              */
+#define DPD_ERR_BUSY (-7)     /* resource in use (e.g. result not ready)            */
+
+#define DPD_WHERE_HOST 0
+#define DPD_WHERE_DEVICE 1
+
+/* Thread-local text of the last failure in this thread ("" if none). */
+DPD_API const char *dpd_last_error(void);
+
+/* Library version string. */
+DPD_API const char *dpd_version(void);
+
+/* ================================================================ one box */
+typedef struct dpd_ctx dpd_ctx;
+
+/* Parameters settable after creation (dpd_set_param). */
+#define DPD_PARAM_KEXP 1          /* weight exponent k in w_R = w^k, (0, 1]; default 1 (Sec. 2.1) */
+#define DPD_PARAM_MASS 2          /* particle mass m > 0; default 1 (Eq. 1) */
+#define DPD_PARAM_BODYFORCE 3     /* constant body force magnitude along DPD_PARAM_FLOW_AXIS */
+#define DPD_PARAM_POISEUILLE_F 4  /* periodic Poiseuille force f (Sec. 4.2): -f where the
+                                     coordinate on DPD_PARAM_GRAD_AXIS is <= L/2, +f above */
+#define DPD_PARAM_FLOW_AXIS 5     /* 0, 1, 2: axis the body force points along; default 2 (z) */
+#define DPD_PARAM_GRAD_AXIS 6     /* 0, 1, 2: axis the Poiseuille force switches on; default 0 (x) */
+#define DPD_PARAM_STENCIL 7       /* DPD_STENCIL_FULL (default) or DPD_STENCIL_HALF */
+
+#define DPD_STENCIL_FULL 0  /* 27 cells, each thread sums its own pairs: no atomics,
+                               bitwise reproducible */
+#define DPD_STENCIL_HALF 1  /* 13 cells + own cell, Newton's third law with atomics
+                               (Sec. 3.2 notes the symmetric form is faster) */
+
+/* Create a context for one periodic box.
+ * box: three edges L_d, each >= 3 rc (so that the 27 neighbour cells are
+ *      distinct) and at most 1023 cells per edge.
+ * a, gamma, kT >= 0; rc > 0; dt > 0; seed: key of the pair noise.
+ * Allocates nothing on the device until dpd_set_state.
+ * Errors: DPD_ERR_ARG (bad value), DPD_ERR_CUDA (no device). */
+DPD_API int dpd_create(dpd_ctx **out, const double box[3], double a, double gamma, double kT, double rc,
+               double dt, uint64_t seed);
+
+/* Release every resource of the context (synchronises its stream). NULL is a no-op. */
+DPD_API int dpd_destroy(dpd_ctx *ctx);
+
+/* Set one DPD_PARAM_* value.  Takes effect at the next dpd_set_state or
+ * dpd_step.  Errors: DPD_ERR_ARG for an unknown key or bad value. */
+DPD_API int dpd_set_param(dpd_ctx *ctx, int key, double value);
+
+/* Enqueue all later work of the context on the given cudaStream_t
+ * (e.g. torch.cuda.current_stream().cuda_stream).  NULL = legacy default stream. */
+DPD_API int dpd_set_stream(dpd_ctx *ctx, void *stream);
+
+/* Load n particles: pos and vel are n x 3 FP32 (positions anywhere; they are
+ * wrapped into [0, L)).  Particle i receives id i, which keys its noise.  The
+ * force at step 0 is computed here; the step counter is reset to 0.
+ * n = 0 is allowed.  Errors: DPD_ERR_ARG, DPD_ERR_NOMEM, DPD_ERR_CUDA. */
+DPD_API int dpd_set_state(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel, int where);
+
+/* Advance nsteps >= 0 steps.  Asynchronous on the context's stream.
+ * Errors: DPD_ERR_STATE before dpd_set_state, DPD_ERR_CUDA. */
+DPD_API int dpd_step(dpd_ctx *ctx, int64_t nsteps);
+
+/* Current positions (in [0, L)) and full-step velocities, n x 3 FP32, in id
+ * order.  Synchronises the stream.  Either pointer may be NULL.
+ * Errors: DPD_ERR_STATE, DPD_ERR_NUMERIC (device flagged non-finite values;
+ * the state is still returned), DPD_ERR_CUDA. */
+DPD_API int dpd_get_state(dpd_ctx *ctx, float *pos, float *vel, int where);
+
+/* Total force on each particle at the current step (pair sum + body force),
+ * n x 3 FP32 in id order.  Synchronises the stream. */
+DPD_API int dpd_get_forces(dpd_ctx *ctx, float *force, int where);
+
+/* Box statistics at the current step, reduced in FP64. */
+typedef struct {
+    double momentum[3];  /* sum m v                                          */
+    double kinetic;      /* sum m v^2 / 2                                    */
+    double kT;           /* 2 kinetic / (3 (N - 1))                          */
+    double virial;       /* sum over pairs i<j of r_ij . F^C_ij              */
+    double pressure;     /* N kT / V + virial / (3 V)                        */
+    int64_t step;        /* steps taken since dpd_set_state                  */
+    int64_t n;           /* particles                                        */
+} dpd_stats;
+
+DPD_API int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out);
+
+/* Number of particles loaded (0 before dpd_set_state). */
+DPD_API int64_t dpd_num_particles(const dpd_ctx *ctx);
+
+/* ------------------------------------------------------- instrumentation */
+#define DPD_NUM_STAGES 5       /* integrate+count, scan, key pass, reorder, force */
+#define DPD_KERNELS_PER_STEP 7 /* kernel launches per step (the scan takes three) */
+
+/* Advance nsteps steps like dpd_step, launching each step's kernels directly
+ * (no graph) with CUDA events recorded on the context's stream between the
+ * stages, synchronising after every step.  stage_ms[DPD_NUM_STAGES] receives
+ * the mean device milliseconds of each stage. */
+DPD_API int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms);
+
+/* ---------------------------------------------------------------- debug */
+/* Raw noise words for n pairs (lo[k], hi[k]) at a step and seed: word 0 of
+ * Philox-4x32-10 on (min, max, step lo, step hi) keyed by (seed lo, seed hi).
+ * lo, hi, out are DEVICE pointers; xi (may be NULL) receives the FP32 noise
+ * values.  Runs on the given stream (NULL = default) and synchronises it. */
+DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uint64_t step, uint64_t seed,
+                  uint32_t *out, float *xi, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPD_H */

@@ -1,0 +1,204 @@
+// C ABI of the single-box context (dpd_*) and the debug entry points.
+#include <cmath>
+#include <cstdint>
+#include <new>
+
+#include "dpd.h"
+#include "engine.h"
+
+namespace dpd {
+const char *last_error_text();
+}
+
+using dpd::BoxParams;
+using dpd::Engine;
+
+struct dpd_ctx {
+  Engine eng;
+  BoxParams bp{};
+  int64_t n = 0;
+  bool loaded = false;
+};
+
+extern "C" {
+
+const char *dpd_last_error(void) { return dpd::last_error_text(); }
+
+const char *dpd_version(void) { return "gb300-dpd 0.1 (sm_103a, Philox-4x32-" "10)"; }
+
+int dpd_create(dpd_ctx **out, const double box[3], double a, double gamma, double kT, double rc,
+               double dt, uint64_t seed) {
+  dpd::clear_error();
+  if (!out || !box) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  *out = nullptr;
+  BoxParams bp{};
+  for (int k = 0; k < 3; ++k) bp.L[k] = box[k];
+  bp.a = a;
+  bp.gamma = gamma;
+  bp.kT = kT;
+  bp.rc = rc;
+  bp.dt = dt;
+  bp.mass = 1.0;
+  bp.kexp = 1.0;
+  bp.fb = 0.0;
+  bp.fb_mode = 0;
+  bp.fb_flow = 2;
+  bp.fb_grad = 0;
+  bp.seed = seed;
+  int ncell[3];
+  int rc_ = dpd::check_params(bp, ncell);
+  if (rc_) return rc_;
+  dpd_ctx *c = new (std::nothrow) dpd_ctx();
+  if (!c) return dpd::set_error(DPD_ERR_NOMEM, "host allocation failed");
+  c->bp = bp;
+  rc_ = c->eng.init();
+  if (rc_) {
+    delete c;
+    return rc_;
+  }
+  *out = c;
+  return DPD_OK;
+}
+
+int dpd_destroy(dpd_ctx *ctx) {
+  delete ctx;
+  return DPD_OK;
+}
+
+int dpd_set_param(dpd_ctx *ctx, int key, double value) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  BoxParams bp = ctx->bp;
+  auto axis = [&](int &dst) -> int {
+    if (!(value == 0.0 || value == 1.0 || value == 2.0))
+      return dpd::set_error(DPD_ERR_ARG, "axis must be 0, 1 or 2");
+    dst = (int)value;
+    return DPD_OK;
+  };
+  int rc = DPD_OK;
+  switch (key) {
+    case DPD_PARAM_KEXP: bp.kexp = value; break;
+    case DPD_PARAM_MASS: bp.mass = value; break;
+    case DPD_PARAM_BODYFORCE:
+      bp.fb = value;
+      bp.fb_mode = (value != 0.0) ? 1 : 0;
+      break;
+    case DPD_PARAM_POISEUILLE_F:
+      bp.fb = value;
+      bp.fb_mode = (value != 0.0) ? 2 : 0;
+      break;
+    case DPD_PARAM_FLOW_AXIS: rc = axis(bp.fb_flow); break;
+    case DPD_PARAM_GRAD_AXIS: rc = axis(bp.fb_grad); break;
+    case DPD_PARAM_STENCIL:
+      if (!(value == DPD_STENCIL_FULL || value == DPD_STENCIL_HALF))
+        return dpd::set_error(DPD_ERR_ARG, "stencil must be DPD_STENCIL_FULL or DPD_STENCIL_HALF");
+      return ctx->eng.set_stencil((int)value);
+    default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
+  }
+  if (rc) return rc;
+  int ncell[3];
+  rc = dpd::check_params(bp, ncell);
+  if (rc) return rc;
+  ctx->bp = bp;
+  if (ctx->loaded) return ctx->eng.update_params({bp});
+  return DPD_OK;
+}
+
+int dpd_set_stream(dpd_ctx *ctx, void *stream) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  return ctx->eng.set_stream((cudaStream_t)stream);
+}
+
+int dpd_set_state(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel, int where) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  if (n < 0 || n > (int64_t)(1 << 30)) return dpd::set_error(DPD_ERR_ARG, "bad particle count");
+  if (where != DPD_WHERE_HOST && where != DPD_WHERE_DEVICE)
+    return dpd::set_error(DPD_ERR_ARG, "where must be DPD_WHERE_HOST or DPD_WHERE_DEVICE");
+  if (n > 0 && (!pos || !vel)) return dpd::set_error(DPD_ERR_ARG, "null position or velocity");
+  ctx->loaded = false;
+  int rc = ctx->eng.layout({ctx->bp}, {n});
+  if (rc) return rc;
+  rc = ctx->eng.load_box(0, pos, vel, where == DPD_WHERE_DEVICE);
+  if (rc) return rc;
+  ctx->eng.set_box_state(0, 0, INT64_MAX / 4);
+  rc = ctx->eng.rebuild();
+  if (rc) return rc;
+  ctx->n = n;
+  ctx->loaded = true;
+  return DPD_OK;
+}
+
+int dpd_step(dpd_ctx *ctx, int64_t nsteps) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  if (!ctx->loaded) return dpd::set_error(DPD_ERR_STATE, "dpd_step before dpd_set_state");
+  return ctx->eng.step(nsteps);
+}
+
+int dpd_get_state(dpd_ctx *ctx, float *pos, float *vel, int where) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  if (!ctx->loaded) return dpd::set_error(DPD_ERR_STATE, "no state loaded");
+  if (where != DPD_WHERE_HOST && where != DPD_WHERE_DEVICE)
+    return dpd::set_error(DPD_ERR_ARG, "bad where");
+  int rc = ctx->eng.gather(0, pos, vel, nullptr, where == DPD_WHERE_DEVICE);
+  if (rc) return rc;
+  return ctx->eng.check_error();
+}
+
+int dpd_get_forces(dpd_ctx *ctx, float *force, int where) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  if (!ctx->loaded) return dpd::set_error(DPD_ERR_STATE, "no state loaded");
+  if (where != DPD_WHERE_HOST && where != DPD_WHERE_DEVICE)
+    return dpd::set_error(DPD_ERR_ARG, "bad where");
+  int rc = ctx->eng.gather(0, nullptr, nullptr, force, where == DPD_WHERE_DEVICE);
+  if (rc) return rc;
+  return ctx->eng.check_error();
+}
+
+int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out) {
+  dpd::clear_error();
+  if (!ctx || !out) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  if (!ctx->loaded) return dpd::set_error(DPD_ERR_STATE, "no state loaded");
+  std::vector<double> s;
+  int rc = ctx->eng.box_sums(s);
+  if (rc) return rc;
+  const BoxParams &bp = ctx->bp;
+  const double m = bp.mass, V = bp.L[0] * bp.L[1] * bp.L[2];
+  const int64_t n = ctx->n;
+  for (int k = 0; k < 3; ++k) out->momentum[k] = m * s[k];
+  out->kinetic = 0.5 * m * s[3];
+  out->kT = (n > 1) ? 2.0 * out->kinetic / (3.0 * (double)(n - 1)) : 0.0;
+  out->virial = 0.5 * s[4];  // each pair was counted by both members
+  out->pressure = (double)n * out->kT / V + out->virial / (3.0 * V);
+  out->step = (int64_t)ctx->eng.box_state(0).step;
+  out->n = n;
+  return ctx->eng.check_error();
+}
+
+int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms) {
+  dpd::clear_error();
+  if (!ctx || !stage_ms) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  if (!ctx->loaded) return dpd::set_error(DPD_ERR_STATE, "no state loaded");
+  if (nsteps < 0) return dpd::set_error(DPD_ERR_ARG, "nsteps must be >= 0");
+  return ctx->eng.profile(nsteps, stage_ms);
+}
+
+int64_t dpd_num_particles(const dpd_ctx *ctx) { return ctx ? ctx->n : 0; }
+
+int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uint64_t step, uint64_t seed,
+                  uint32_t *out, float *xi, void *stream) {
+  dpd::clear_error();
+  if (n < 0) return dpd::set_error(DPD_ERR_ARG, "negative count");
+  if (n == 0) return DPD_OK;
+  if (!lo || !hi || !out) return dpd::set_error(DPD_ERR_ARG, "null device pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  DPD_CUDA_TRY(dpd::launch_debug_rng(lo, hi, n, step, seed, out, xi, s));
+  DPD_CUDA_TRY(cudaStreamSynchronize(s));
+  return DPD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Device-side definitions of the DPD fluid step: per-box descriptors, the
+// pair-noise generator and small geometry helpers.
+//
+// Data layout in HBM (one packed set of boxes; a single box is the case
+// nbox = 1):
+//   pos[p]  float4 (x, y, z, id)     id = box-local particle id as int bits
+//   vel[p]  float4 (vx, vy, vz, cell) cell = packed local cell coordinates
+//   frc[p]  float4 (fx, fy, fz, vir)  vir = sum over this particle's pairs of
+//                                     r . F^C (both members count the pair)
+// Particles of box b occupy slots [pbase[b], pbase[b+1]) and, after every
+// rebuild, appear in cell order (cell = cellBase[b] + (cz*ny + cy)*nx + cx).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpd {
+
+// Pair noise: Philox-4x32-R (Salmon, Moraes, Dror, Shaw, SC'11).
+#ifndef DPD_PHILOX_ROUNDS
+#define DPD_PHILOX_ROUNDS 10
+#endif
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;  // round multipliers
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;  // Weyl key increments
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+constexpr int kCellBits = 10;                 // packed cell coords: 10 bits per axis
+constexpr int kMaxCellsPerAxis = (1 << kCellBits) - 1;
+
+// Error bits raised by kernels into the context's device error word.
+constexpr unsigned kErrNonFinite = 1u;        // a position or velocity is NaN/Inf
+constexpr unsigned kErrRunaway = 2u;          // a particle moved more than one box edge
+
+// Constants of one periodic box (read-only during a step).
+struct BoxDev {
+  float L[3];       // box edges
+  float invh[3];    // cells per unit length, n_d / L_d
+  int n[3];         // cells per axis, floor(L_d / rc) >= 3
+  int cellBase;     // first packed cell index of this box
+  int pbase;        // first particle slot of this box
+  int np;           // particles in this box
+  float a;          // conservative coefficient (Eq. 3)
+  float gamma;      // dissipative coefficient (Eq. 5)
+  float sig;        // sigma * sqrt(3) * 2^-24 / sqrt(dt): multiplies the integer noise
+  float rc2;        // rc^2
+  float inv_rc;     // 1 / rc
+  float kexp;       // weight exponent k, w_R = w^k
+  float hdt_m;      // dt / (2 m)
+  float dt;         // time step
+  float fb;         // body-force magnitude
+  int fb_mode;      // 0 none, 1 constant, 2 periodic Poiseuille (Sec. 4.2)
+  int fb_flow;      // axis of the body force
+  int fb_grad;      // axis on which the Poiseuille force switches sign
+  float fb_half;    // L[fb_grad] / 2
+  uint32_t seed_lo; // noise key
+  uint32_t seed_hi;
+  int pad_;
+};
+
+// Mutable per-box step state (device resident so that graphs can replay it).
+struct BoxState {
+  unsigned long long step;  // noise step index of the force held in frc
+  long long remaining;      // steps still to take; 0 freezes the box
+  int pending;              // 1: vel holds v(n - 1/2); the full-step velocity is vel + hdt_m f
+  int adv;                  // 1: the box is being advanced / needs its force this step
+};
+
+// ---------------------------------------------------------------- noise
+// Word 0 of Philox-4x32-R on counter (c0, c1, c2, c3) and key (k0, k1).
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < DPD_PHILOX_ROUNDS; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return c0;
+}
+
+// Signed odd integer t = 2 (u >> 8) + 1 - 2^24, exactly representable in FP32;
+// xi = sqrt(3) (2U - 1) = sqrt(3) t 2^-24 with U = ((u >> 8) + 1/2) 2^-24.
+__device__ __forceinline__ float noise_int(uint32_t u) {
+  const int t = (int)((u >> 8) * 2u + 1u) - (1 << 24);
+  return __int2float_rn(t);
+}
+
+__device__ __forceinline__ uint32_t pair_word(uint32_t ida, uint32_t idb, uint32_t step_lo,
+                                              uint32_t step_hi, uint32_t seed_lo,
+                                              uint32_t seed_hi) {
+  const uint32_t lo = min(ida, idb), hi = max(ida, idb);
+  return philox_word0(lo, hi, step_lo, step_hi, seed_lo, seed_hi);
+}
+
+// ---------------------------------------------------------------- geometry
+// Fold a coordinate that moved by less than one edge back into [0, L).
+__device__ __forceinline__ float wrap_coord(float x, float L) {
+  if (x < 0.0f) {
+    x += L;
+  } else if (x >= L) {
+    x -= L;
+  }
+  if (x >= L) x = 0.0f;  // a tiny negative x + L can round up to L
+  return x;
+}
+
+__device__ __forceinline__ int cell_axis(float x, float invh, int n) {
+  int c = __float2int_rz(__fmul_rn(x, invh));
+  return min(max(c, 0), n - 1);
+}
+
+__device__ __forceinline__ int pack_cell(int cx, int cy, int cz) {
+  return cx | (cy << kCellBits) | (cz << (2 * kCellBits));
+}
+
+__device__ __forceinline__ void unpack_cell(int c, int &cx, int &cy, int &cz) {
+  cx = c & kMaxCellsPerAxis;
+  cy = (c >> kCellBits) & kMaxCellsPerAxis;
+  cz = (c >> (2 * kCellBits)) & kMaxCellsPerAxis;
+}
+
+// Largest b with pbase[b] <= p (pbase has nbox + 1 entries, non-decreasing).
+__device__ __forceinline__ int find_box(const int *__restrict__ pbase, int nbox, int p) {
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pbase + mid) <= p)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace dpd

@@ -1,0 +1,510 @@
+// Engine implementation: device buffers, the per-step launch sequence, CUDA
+// graph capture of step chunks, and the FP64 statistics reduction.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "dpd.h"
+
+namespace dpd {
+
+static thread_local std::string t_err;
+
+int set_error(int code, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+void clear_error() { t_err.clear(); }
+const char *last_error_text() { return t_err.c_str(); }
+
+int check_params(const BoxParams &bp, int n[3]) {
+  if (!(bp.rc > 0.0) || !std::isfinite(bp.rc)) return set_error(DPD_ERR_ARG, "rc must be > 0");
+  double cells = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    if (!std::isfinite(bp.L[k]) || !(bp.L[k] >= 3.0 * bp.rc))
+      return set_error(DPD_ERR_ARG, "box edge %d = %g must be >= 3 rc = %g", k, bp.L[k],
+                       3.0 * bp.rc);
+    const double nd = std::floor(bp.L[k] / bp.rc);
+    if (nd > kMaxCellsPerAxis)
+      return set_error(DPD_ERR_ARG, "box edge %d spans %g cells; at most %d per axis", k, nd,
+                       kMaxCellsPerAxis);
+    n[k] = (int)nd;
+    cells *= nd;
+  }
+  if (cells > (double)(1 << 30)) return set_error(DPD_ERR_ARG, "too many cells (%g)", cells);
+  auto nonneg = [](double v) { return std::isfinite(v) && v >= 0.0; };
+  if (!nonneg(bp.a)) return set_error(DPD_ERR_ARG, "a must be >= 0");
+  if (!nonneg(bp.gamma)) return set_error(DPD_ERR_ARG, "gamma must be >= 0");
+  if (!nonneg(bp.kT)) return set_error(DPD_ERR_ARG, "kT must be >= 0");
+  if (!(bp.dt > 0.0) || !std::isfinite(bp.dt)) return set_error(DPD_ERR_ARG, "dt must be > 0");
+  if (!(bp.mass > 0.0) || !std::isfinite(bp.mass))
+    return set_error(DPD_ERR_ARG, "mass must be > 0");
+  if (!(bp.kexp > 0.0 && bp.kexp <= 1.0))
+    return set_error(DPD_ERR_ARG, "weight exponent k must be in (0, 1]");
+  if (bp.fb_mode < 0 || bp.fb_mode > 2 || !std::isfinite(bp.fb))
+    return set_error(DPD_ERR_ARG, "bad body force");
+  if (bp.fb_flow < 0 || bp.fb_flow > 2 || bp.fb_grad < 0 || bp.fb_grad > 2)
+    return set_error(DPD_ERR_ARG, "body-force axes must be 0, 1 or 2");
+  return DPD_OK;
+}
+
+BoxDev make_box_dev(const BoxParams &bp, int cellBase, int pbase, int np) {
+  BoxDev d{};
+  int n[3];
+  for (int k = 0; k < 3; ++k) {
+    n[k] = (int)std::floor(bp.L[k] / bp.rc);
+    d.L[k] = (float)bp.L[k];
+    d.n[k] = n[k];
+    d.invh[k] = (float)((double)n[k] / bp.L[k]);
+  }
+  d.cellBase = cellBase;
+  d.pbase = pbase;
+  d.np = np;
+  d.a = (float)bp.a;
+  d.gamma = (float)bp.gamma;
+  const double sigma = std::sqrt(2.0 * bp.gamma * bp.kT);  // fluctuation-dissipation
+  d.sig = (float)(sigma * std::sqrt(3.0) / 16777216.0 / std::sqrt(bp.dt));
+  d.rc2 = (float)(bp.rc * bp.rc);
+  d.inv_rc = (float)(1.0 / bp.rc);
+  d.kexp = (float)bp.kexp;
+  d.hdt_m = (float)(0.5 * bp.dt / bp.mass);
+  d.dt = (float)bp.dt;
+  d.fb = (float)bp.fb;
+  d.fb_mode = bp.fb_mode;
+  d.fb_flow = bp.fb_flow;
+  d.fb_grad = bp.fb_grad;
+  d.fb_half = (float)(0.5 * bp.L[bp.fb_grad]);
+  d.seed_lo = (uint32_t)(bp.seed & 0xffffffffu);
+  d.seed_hi = (uint32_t)(bp.seed >> 32);
+  return d;
+}
+
+// ------------------------------------------------------------------ engine
+Engine::Engine() {}
+
+Engine::~Engine() {
+  if (device_ >= 0) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != device_) cudaSetDevice(device_);
+    // No stream synchronisation here: the caller's stream may already be
+    // gone; cudaFree waits for the device, and an in-flight graph is freed
+    // when it completes.
+    drop_graph();
+    free_all();
+    if (d_.err) cudaFree(d_.err);
+    if (cap_) cudaStreamDestroy(cap_);
+    if (cur >= 0 && cur != device_) cudaSetDevice(cur);
+  }
+}
+
+int Engine::init() {
+  int dev = -1;
+  DPD_CUDA_TRY(cudaGetDevice(&dev));
+  int count = 0;
+  DPD_CUDA_TRY(cudaGetDeviceCount(&count));
+  if (count <= 0) return set_error(DPD_ERR_CUDA, "no CUDA device");
+  device_ = dev;
+  static std::mutex mu;
+  static bool prepared[256] = {false};
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 256 && !prepared[dev]) {
+      DPD_CUDA_TRY(prepare_device());
+      prepared[dev] = true;
+    }
+  }
+  DPD_CUDA_TRY(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+  DPD_CUDA_TRY(cudaMalloc(&d_.err, sizeof(unsigned)));
+  DPD_CUDA_TRY(cudaMemset(d_.err, 0, sizeof(unsigned)));
+  return DPD_OK;
+}
+
+int Engine::set_stream(cudaStream_t s) {
+  stream_ = s;
+  return DPD_OK;
+}
+
+int Engine::set_stencil(int stencil) {
+  if (stencil != 0 && stencil != 1) return set_error(DPD_ERR_ARG, "stencil must be 0 or 1");
+  if (stencil != stencil_) {
+    stencil_ = stencil;
+    drop_graph();
+  }
+  return DPD_OK;
+}
+
+void Engine::drop_graph() {
+  if (graph_) {
+    cudaGraphExecDestroy(graph_);
+    graph_ = nullptr;
+  }
+}
+
+int Engine::free_all() {
+  void *ptrs[] = {d_.pos,   d_.vel,    d_.frc,   d_.pos2,  d_.vel2,  d_.cellOf, d_.slotIn,
+                  d_.keyTmp, d_.count, d_.start, d_.bsum,  d_.boxes, d_.pbase,  d_.st,
+                  d_.work,  d_.part};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  unsigned *err = d_.err;  // the error word lives as long as the engine
+  d_ = DeviceArrays{};
+  d_.err = err;
+  return DPD_OK;
+}
+
+size_t Engine::device_bytes() const {
+  return d_.capP * (5 * sizeof(float4) + 3 * sizeof(int)) +
+         d_.capC * 2 * sizeof(int) + (d_.capC / kScanTile + 1) * sizeof(int) +
+         d_.capB * (sizeof(BoxDev) + sizeof(int) + sizeof(BoxState)) +
+         d_.capW * (sizeof(StatsWork) + kStatsFields * sizeof(double));
+}
+
+template <typename T>
+static cudaError_t grow(T *&ptr, size_t n) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  return cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+int Engine::reserve(size_t np, size_t nc, size_t nb) {
+  if (np > d_.capP) {
+    drop_graph();
+    const size_t cap = std::max(np, d_.capP + d_.capP / 4);
+    DPD_CUDA_TRY(grow(d_.pos, cap));
+    DPD_CUDA_TRY(grow(d_.vel, cap));
+    DPD_CUDA_TRY(grow(d_.frc, cap));
+    DPD_CUDA_TRY(grow(d_.pos2, cap));
+    DPD_CUDA_TRY(grow(d_.vel2, cap));
+    DPD_CUDA_TRY(grow(d_.cellOf, cap));
+    DPD_CUDA_TRY(grow(d_.slotIn, cap));
+    DPD_CUDA_TRY(grow(d_.keyTmp, cap));
+    DPD_CUDA_TRY(cudaMemset(d_.frc, 0, cap * sizeof(float4)));
+    d_.capP = cap;
+  }
+  const size_t tiles = (size_t)scan_tiles((int)nc);
+  const size_t ncap = tiles * kScanTile;
+  if (ncap > d_.capC) {
+    drop_graph();
+    if (tiles > (size_t)kScanMaxTiles)
+      return set_error(DPD_ERR_ARG, "too many cells for one scan (%zu)", nc);
+    DPD_CUDA_TRY(grow(d_.count, ncap));
+    DPD_CUDA_TRY(grow(d_.start, ncap));
+    DPD_CUDA_TRY(grow(d_.bsum, tiles));
+    DPD_CUDA_TRY(cudaMemset(d_.count, 0, ncap * sizeof(int)));
+    d_.capC = ncap;
+  }
+  if (nb > d_.capB) {
+    drop_graph();
+    const size_t cap = std::max(nb, d_.capB * 2);
+    DPD_CUDA_TRY(grow(d_.boxes, cap));
+    DPD_CUDA_TRY(grow(d_.pbase, cap + 1));
+    DPD_CUDA_TRY(grow(d_.st, cap));
+    d_.capB = cap;
+  }
+  return DPD_OK;
+}
+
+Packed Engine::packed() const {
+  Packed P{};
+  P.pos = d_.pos;
+  P.vel = d_.vel;
+  P.frc = d_.frc;
+  P.pos2 = d_.pos2;
+  P.vel2 = d_.vel2;
+  P.cellOf = d_.cellOf;
+  P.slotIn = d_.slotIn;
+  P.keyTmp = d_.keyTmp;
+  P.count = d_.count;
+  P.start = d_.start;
+  P.bsum = d_.bsum;
+  P.boxes = d_.boxes;
+  P.pbase = d_.pbase;
+  P.st = d_.st;
+  P.err = d_.err;
+  P.ntot = ntot_;
+  P.ncell = ncell_;
+  P.nbox = (int)boxes_.size();
+  if (!boxes_.empty()) P.single = boxes_[0];
+  return P;
+}
+
+int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64_t> &np) {
+  if (params.size() != np.size() || params.empty())
+    return set_error(DPD_ERR_ARG, "layout needs one particle count per box");
+  std::vector<BoxDev> boxes(params.size());
+  std::vector<int> pbase(params.size() + 1);
+  int64_t ptot = 0, ctot = 0;
+  for (size_t b = 0; b < params.size(); ++b) {
+    int n[3];
+    int rc = check_params(params[b], n);
+    if (rc) return rc;
+    if (np[b] < 0) return set_error(DPD_ERR_ARG, "negative particle count");
+    pbase[b] = (int)ptot;
+    boxes[b] = make_box_dev(params[b], (int)ctot, (int)ptot, (int)np[b]);
+    ptot += np[b];
+    ctot += (int64_t)n[0] * n[1] * n[2];
+    if (ptot > (int64_t)(1 << 30) || ctot > (int64_t)(1 << 30))
+      return set_error(DPD_ERR_ARG, "packed set too large (%lld particles, %lld cells)",
+                       (long long)ptot, (long long)ctot);
+  }
+  pbase[params.size()] = (int)ptot;
+  int rc = reserve((size_t)ptot, (size_t)ctot, params.size());
+  if (rc) return rc;
+  params_ = params;
+  boxes_ = boxes;
+  pbase_ = pbase;
+  ntot_ = (int)ptot;
+  ncell_ = (int)ctot;
+  st_host_.assign(params.size(), BoxState{0ull, 0ll, 0, 0});
+  work_dirty_ = true;
+  drop_graph();
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_.boxes, boxes_.data(), boxes_.size() * sizeof(BoxDev),
+                               cudaMemcpyHostToDevice, stream_));
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_.pbase, pbase_.data(), pbase_.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, stream_));
+  return DPD_OK;
+}
+
+int Engine::update_params(const std::vector<BoxParams> &params) {
+  if (params.size() != boxes_.size()) return set_error(DPD_ERR_ARG, "box count changed");
+  for (size_t b = 0; b < params.size(); ++b) {
+    int n[3];
+    int rc = check_params(params[b], n);
+    if (rc) return rc;
+    const BoxDev nb = make_box_dev(params[b], boxes_[b].cellBase, boxes_[b].pbase, boxes_[b].np);
+    if (nb.n[0] != boxes_[b].n[0] || nb.n[1] != boxes_[b].n[1] || nb.n[2] != boxes_[b].n[2])
+      return set_error(DPD_ERR_ARG, "box edges or rc changed the cell grid; reload the state");
+    boxes_[b] = nb;
+  }
+  params_ = params;
+  drop_graph();
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_.boxes, boxes_.data(), boxes_.size() * sizeof(BoxDev),
+                               cudaMemcpyHostToDevice, stream_));
+  return DPD_OK;
+}
+
+int Engine::load_box(int box, const float *pos, const float *vel, bool device_ptr) {
+  if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
+  const int n = pbase_[box + 1] - pbase_[box];
+  if (n == 0) return DPD_OK;
+  if (!pos || !vel) return set_error(DPD_ERR_ARG, "null position or velocity array");
+  const float *p3 = pos, *v3 = vel;
+  if (!device_ptr) {
+    float *sp = reinterpret_cast<float *>(d_.pos2), *sv = reinterpret_cast<float *>(d_.vel2);
+    DPD_CUDA_TRY(cudaMemcpyAsync(sp, pos, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                                 stream_));
+    DPD_CUDA_TRY(cudaMemcpyAsync(sv, vel, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                                 stream_));
+    p3 = sp;
+    v3 = sv;
+  }
+  const BoxDev &B = boxes_[box];
+  DPD_CUDA_TRY(launch_load(packed(), pbase_[box], n, p3, v3, B.L[0], B.L[1], B.L[2], stream_));
+  return DPD_OK;
+}
+
+void Engine::set_box_state(int box, uint64_t step0, int64_t remaining) {
+  st_host_[box] = BoxState{step0, remaining, 0, 1};
+}
+
+int Engine::set_remaining(int box, int64_t remaining) {
+  if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
+  st_host_[box].remaining = remaining;
+  DPD_CUDA_TRY(cudaMemcpyAsync(&d_.st[box].remaining, &st_host_[box].remaining,
+                               sizeof(long long), cudaMemcpyHostToDevice, stream_));
+  return DPD_OK;
+}
+
+int Engine::rebuild() {
+  for (auto &s : st_host_) s.adv = 1;
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_.st, st_host_.data(), st_host_.size() * sizeof(BoxState),
+                               cudaMemcpyHostToDevice, stream_));
+  DPD_CUDA_TRY(launch_step(packed(), false, false, stencil_, stream_));
+  return DPD_OK;
+}
+
+int Engine::capture_graph() {
+  drop_graph();
+  const Packed P = packed();
+  cudaGraph_t g = nullptr;
+  DPD_CUDA_TRY(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < graph_chunk && e == cudaSuccess; ++k)
+    e = launch_step(P, true, true, stencil_, cap_);
+  cudaError_t e2 = cudaStreamEndCapture(cap_, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return set_error(DPD_ERR_CUDA, "graph capture failed: %s",
+                     cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&graph_, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    graph_ = nullptr;
+    return set_error(DPD_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  return DPD_OK;
+}
+
+int Engine::step(int64_t nsteps) {
+  if (nsteps < 0) return set_error(DPD_ERR_ARG, "nsteps must be >= 0");
+  if (ntot_ == 0 || nsteps == 0) {
+    for (auto &s : st_host_) {
+      const int64_t k = std::min<int64_t>(s.remaining, nsteps);
+      s.step += (unsigned long long)k;
+      s.remaining -= k;
+      if (k > 0) s.pending = 1;
+    }
+    if (ntot_ == 0 && nsteps > 0) {
+      DPD_CUDA_TRY(cudaMemcpyAsync(d_.st, st_host_.data(), st_host_.size() * sizeof(BoxState),
+                                   cudaMemcpyHostToDevice, stream_));
+    }
+    return DPD_OK;
+  }
+  int64_t left = nsteps;
+  if (graph_chunk > 1 && left >= graph_chunk) {
+    if (!graph_) {
+      int rc = capture_graph();
+      if (rc) return rc;
+    }
+    while (left >= graph_chunk) {
+      DPD_CUDA_TRY(cudaGraphLaunch(graph_, stream_));
+      left -= graph_chunk;
+    }
+  }
+  const Packed P = packed();
+  for (int64_t k = 0; k < left; ++k) DPD_CUDA_TRY(launch_step(P, true, true, stencil_, stream_));
+  for (auto &s : st_host_) {
+    const int64_t k = std::min<int64_t>(s.remaining, nsteps);
+    s.step += (unsigned long long)k;
+    s.remaining -= k;
+    if (k > 0) s.pending = 1;
+  }
+  return DPD_OK;
+}
+
+int Engine::profile(int64_t nsteps, double *stage_ms) {
+  for (int k = 0; k < kNumStages; ++k) stage_ms[k] = 0.0;
+  if (nsteps <= 0 || ntot_ == 0) return step(nsteps);
+  cudaEvent_t ev[kNumStages + 1] = {};
+  for (auto &e : ev) DPD_CUDA_TRY(cudaEventCreate(&e));
+  const Packed P = packed();
+  int rc = DPD_OK;
+  for (int64_t s = 0; s < nsteps && rc == DPD_OK; ++s) {
+    cudaError_t e = launch_step_timed(P, stencil_, stream_, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[kNumStages]);
+    if (e != cudaSuccess) {
+      rc = set_error(DPD_ERR_CUDA, "profiled step: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (int k = 0; k < kNumStages; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      stage_ms[k] += ms / (double)nsteps;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (auto &st : st_host_) {
+    const int64_t k = std::min<int64_t>(st.remaining, nsteps);
+    st.step += (unsigned long long)k;
+    st.remaining -= k;
+    if (k > 0) st.pending = 1;
+  }
+  return DPD_OK;
+}
+
+int Engine::sync() {
+  DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  return DPD_OK;
+}
+
+int Engine::check_error() {
+  unsigned h = 0;
+  DPD_CUDA_TRY(cudaMemcpyAsync(&h, d_.err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+  DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  if (h) {
+    DPD_CUDA_TRY(cudaMemsetAsync(d_.err, 0, sizeof(unsigned), stream_));
+    return set_error(DPD_ERR_NUMERIC, "device flagged %s%s",
+                     (h & kErrNonFinite) ? "non-finite positions/velocities " : "",
+                     (h & kErrRunaway) ? "a particle moving more than one box edge per step" : "");
+  }
+  return DPD_OK;
+}
+
+int Engine::gather(int box, float *pos, float *vel, float *frc, bool device_ptr) {
+  if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
+  const int n = pbase_[box + 1] - pbase_[box];
+  if (n == 0) return DPD_OK;
+  const Packed P = packed();
+  if (device_ptr) {
+    DPD_CUDA_TRY(launch_gather(P, box, pbase_[box], n, pos, vel, frc, stream_));
+    DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+    return DPD_OK;
+  }
+  float *sp = reinterpret_cast<float *>(d_.pos2), *sv = reinterpret_cast<float *>(d_.vel2);
+  const size_t bytes = (size_t)n * 3 * sizeof(float);
+  if (pos || vel) {
+    DPD_CUDA_TRY(launch_gather(P, box, pbase_[box], n, pos ? sp : nullptr, vel ? sv : nullptr,
+                               nullptr, stream_));
+    if (pos) DPD_CUDA_TRY(cudaMemcpyAsync(pos, sp, bytes, cudaMemcpyDeviceToHost, stream_));
+    if (vel) DPD_CUDA_TRY(cudaMemcpyAsync(vel, sv, bytes, cudaMemcpyDeviceToHost, stream_));
+  }
+  if (frc) {
+    DPD_CUDA_TRY(launch_gather(P, box, pbase_[box], n, nullptr, nullptr, sp, stream_));
+    DPD_CUDA_TRY(cudaMemcpyAsync(frc, sp, bytes, cudaMemcpyDeviceToHost, stream_));
+  }
+  DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  return DPD_OK;
+}
+
+int Engine::box_sums(std::vector<double> &sums) {
+  const int nb = nbox();
+  constexpr int kChunk = 32768;
+  if (work_dirty_) {
+    work_.clear();
+    for (int b = 0; b < nb; ++b) {
+      const int s0 = pbase_[b], s1 = pbase_[b + 1];
+      if (s1 == s0) {
+        work_.push_back(StatsWork{b, s0, s0, 0});
+        continue;
+      }
+      for (int s = s0; s < s1; s += kChunk) work_.push_back(StatsWork{b, s, std::min(s + kChunk, s1), 0});
+    }
+    if (work_.size() > d_.capW) {
+      if (d_.work) cudaFree(d_.work);
+      if (d_.part) cudaFree(d_.part);
+      d_.work = nullptr;
+      d_.part = nullptr;
+      const size_t cap = work_.size() * 2;
+      DPD_CUDA_TRY(cudaMalloc(&d_.work, cap * sizeof(StatsWork)));
+      DPD_CUDA_TRY(cudaMalloc(&d_.part, cap * kStatsFields * sizeof(double)));
+      d_.capW = cap;
+    }
+    DPD_CUDA_TRY(cudaMemcpyAsync(d_.work, work_.data(), work_.size() * sizeof(StatsWork),
+                                 cudaMemcpyHostToDevice, stream_));
+    work_dirty_ = false;
+  }
+  std::vector<double> part(work_.size() * kStatsFields);
+  DPD_CUDA_TRY(launch_stats(packed(), d_.work, (int)work_.size(), d_.part, stream_));
+  DPD_CUDA_TRY(cudaMemcpyAsync(part.data(), d_.part, part.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, stream_));
+  DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  sums.assign((size_t)nb * kStatsFields, 0.0);
+  for (size_t w = 0; w < work_.size(); ++w)
+    for (int k = 0; k < kStatsFields; ++k)
+      sums[(size_t)work_[w].box * kStatsFields + k] += part[w * kStatsFields + k];
+  return DPD_OK;
+}
+
+}  // namespace dpd

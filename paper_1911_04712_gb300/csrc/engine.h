@@ -1,0 +1,129 @@
+// Engine: device memory, launch sequence and CUDA-graph replay for one packed
+// set of periodic DPD boxes.  The single-box context, the multi-box batch and
+// the request queue all drive an Engine.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dpd_device.cuh"
+#include "kernels.h"
+
+namespace dpd {
+
+// Records a message for dpd_last_error() and returns `code`.
+int set_error(int code, const char *fmt, ...);
+void clear_error();
+
+#define DPD_CUDA_TRY(expr)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return ::dpd::set_error(e_ == cudaErrorMemoryAllocation ? -2 : -3, "%s: %s (%s:%d)", \
+                              #expr, cudaGetErrorString(e_), __FILE__, __LINE__);           \
+  } while (0)
+
+// Host description of one box.
+struct BoxParams {
+  double L[3];
+  double a, gamma, kT, rc, dt, mass, kexp;
+  double fb;        // body force magnitude
+  int fb_mode;      // 0 none, 1 constant, 2 periodic Poiseuille
+  int fb_flow, fb_grad;
+  uint64_t seed;
+};
+
+// Validates the parameters and derives the cell grid; returns DPD_OK or DPD_ERR_ARG.
+int check_params(const BoxParams &bp, int n_out[3]);
+
+BoxDev make_box_dev(const BoxParams &bp, int cellBase, int pbase, int np);
+
+struct DeviceArrays {
+  float4 *pos = nullptr, *vel = nullptr, *frc = nullptr, *pos2 = nullptr, *vel2 = nullptr;
+  int *cellOf = nullptr, *slotIn = nullptr, *keyTmp = nullptr;
+  int *count = nullptr, *start = nullptr, *bsum = nullptr;
+  BoxDev *boxes = nullptr;
+  int *pbase = nullptr;
+  BoxState *st = nullptr;
+  unsigned *err = nullptr;
+  StatsWork *work = nullptr;
+  double *part = nullptr;
+  size_t capP = 0, capC = 0, capB = 0, capW = 0;
+};
+
+class Engine {
+ public:
+  Engine();
+  ~Engine();
+  Engine(const Engine &) = delete;
+  Engine &operator=(const Engine &) = delete;
+
+  int init();                       // binds the current device, prepares kernels
+  int set_stream(cudaStream_t s);
+  int set_stencil(int stencil);
+
+  // Lay out boxes: particle counts per box decide the slot ranges.  Allocates
+  // (or grows) device memory and uploads descriptors.  Box state is reset.
+  int layout(const std::vector<BoxParams> &params, const std::vector<int64_t> &np);
+  // Re-upload descriptors after a parameter change (same layout).
+  int update_params(const std::vector<BoxParams> &params);
+
+  // Load particles of one box (n x 3 host or device arrays).
+  int load_box(int box, const float *pos, const float *vel, bool device_ptr);
+  // Host mirror of a box's step state; takes effect at the next rebuild().
+  void set_box_state(int box, uint64_t step0, int64_t remaining);
+  // Cell-list build and force at each box's current step, without moving
+  // particles (used after loading).  Boxes that were not reloaded keep their
+  // order and get the same force again.
+  int rebuild();
+  const BoxState &box_state(int b) const { return st_host_[b]; }
+  // Change how many steps a box may still take (0 freezes it); uploads at once.
+  int set_remaining(int box, int64_t remaining);
+
+  int step(int64_t nsteps);         // enqueue nsteps steps (graph chunks + direct launches)
+  // Run nsteps steps with per-stage CUDA events (synchronising after each
+  // step); adds the mean milliseconds of each stage to stage_ms[kNumStages].
+  int profile(int64_t nsteps, double *stage_ms);
+  int sync();
+  int check_error();                // reads and clears the device error word
+
+  int gather(int box, float *pos, float *vel, float *frc, bool device_ptr);
+  // FP64 partial sums per box: {sum v (3), sum v^2, sum frc.w, count}.
+  int box_sums(std::vector<double> &sums);
+
+  int nbox() const { return (int)boxes_.size(); }
+  int ntot() const { return ntot_; }
+  int ncell() const { return ncell_; }
+  int64_t box_n(int b) const { return pbase_[b + 1] - pbase_[b]; }
+  const BoxParams &params(int b) const { return params_[b]; }
+  cudaStream_t stream() const { return stream_; }
+  size_t device_bytes() const;
+  int graph_chunk = 32;             // steps per captured graph
+
+ private:
+  Packed packed() const;
+  int reserve(size_t np, size_t nc, size_t nb);
+  int free_all();
+  int capture_graph();
+  void drop_graph();
+
+  int device_ = -1;
+  cudaStream_t stream_ = nullptr;   // caller's stream (nullptr: legacy default)
+  cudaStream_t cap_ = nullptr;      // private stream used to capture graphs
+  int stencil_ = 0;
+  std::vector<BoxParams> params_;
+  std::vector<BoxDev> boxes_;
+  std::vector<int> pbase_;
+  std::vector<BoxState> st_host_;   // host mirror of the device box states
+  int ntot_ = 0, ncell_ = 0;
+  DeviceArrays d_;
+  std::vector<StatsWork> work_;
+  bool work_dirty_ = true;
+  cudaGraphExec_t graph_ = nullptr;
+};
+
+}  // namespace dpd

@@ -1,0 +1,73 @@
+// Host-side launchers of the DPD kernels (kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dpd_device.cuh"
+
+namespace dpd {
+
+// Device pointers and sizes of one packed set of boxes.  Passed by value to
+// every kernel.  `single` duplicates boxes[0] when nbox == 1 so that the
+// single-box kernels read box constants from the parameter bank.
+struct Packed {
+  float4 *pos, *vel, *frc;     // primary arrays, cell order
+  float4 *pos2, *vel2;         // integrated copies before the reorder; staging
+  int *cellOf;                 // packed global cell of each slot (pre-reorder order)
+  int *slotIn;                 // arrival rank of each slot inside its cell
+  int *keyTmp;                 // old slot index at each arrival position
+  int *count;                  // particles per cell (zeroed by the scan)
+  int *start;                  // exclusive scan of count, ncell + 1 entries
+  int *bsum;                   // per-tile sums of the scan
+  const BoxDev *boxes;
+  const int *pbase;            // nbox + 1 entries
+  BoxState *st;
+  unsigned *err;
+  int ntot, ncell, nbox;
+  BoxDev single;
+};
+
+struct StatsWork {  // one block of the statistics reduction
+  int box, begin, end, pad;
+};
+constexpr int kStatsFields = 6;  // sum v (3), sum v^2, sum frc.w, count
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;  // cells per scan tile
+constexpr int kScanMaxTiles = 1024 * 16;              // one block scans up to this many tile sums
+
+inline int scan_tiles(int ncell) { return (ncell + 1 + kScanTile - 1) / kScanTile; }
+
+// Set per-function launch attributes on the current device (once per device,
+// before any capture).
+cudaError_t prepare_device();
+
+// Convert n x 3 inputs of one box into float4 slots (ids 0..n-1, wrapped).
+cudaError_t launch_load(const Packed &P, int box_slot0, int n, const float *pos3, const float *vel3,
+                        float Lx, float Ly, float Lz, cudaStream_t s);
+
+// One step (move = true) or the initial rebuild (move = false):
+// kick/drift/wrap + cell count, scan, reorder, force.
+cudaError_t launch_step(const Packed &P, bool move, bool advance, int stencil, cudaStream_t s);
+
+// One step with events recorded around its stages: ev[0] before the
+// integrate/count kernel, then after it, after the scan, after the key pass,
+// after the reorder and after the force kernel (6 events).
+cudaError_t launch_step_timed(const Packed &P, int stencil, cudaStream_t s, cudaEvent_t *ev);
+constexpr int kNumStages = 5;
+constexpr int kKernelsPerStep = 7;
+
+// Per-work-item FP64 partial sums for box statistics.
+cudaError_t launch_stats(const Packed &P, const StatsWork *work, int nwork, double *out,
+                         cudaStream_t s);
+
+// Write slots [slot0, slot0 + n) to id order as n x 3 arrays (any may be null);
+// velocities are full-step (pending half kick applied).
+cudaError_t launch_gather(const Packed &P, int box, int slot0, int n, float *pos3, float *vel3,
+                          float *frc3, cudaStream_t s);
+
+cudaError_t launch_debug_rng(const uint32_t *lo, const uint32_t *hi, long long n, uint64_t step,
+                             uint64_t seed, uint32_t *out, float *xi, cudaStream_t s);
+
+}  // namespace dpd

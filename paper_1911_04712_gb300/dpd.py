@@ -1,0 +1,253 @@
+"""Python binding of libdpd.so: argument marshalling only.
+
+Every step of the DPD fluid update runs in the library's CUDA kernels.  This
+module converts arrays to pointers (NumPy arrays become host pointers, CUDA
+torch tensors become device pointers), checks status codes and raises
+``DPDError`` with the library's message.  There is no CPU fallback: if the
+shared library is missing, importing the binding's entry points raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdpd.so")
+
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_STATE, ERR_NUMERIC, ERR_TIMEOUT, ERR_BUSY = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+WHERE_HOST, WHERE_DEVICE = 0, 1
+PARAM_KEXP, PARAM_MASS, PARAM_BODYFORCE, PARAM_POISEUILLE_F = 1, 2, 3, 4
+PARAM_FLOW_AXIS, PARAM_GRAD_AXIS, PARAM_STENCIL = 5, 6, 7
+STENCIL_FULL, STENCIL_HALF = 0, 1
+NUM_STAGES, KERNELS_PER_STEP = 5, 7
+STAGE_NAMES = ("integrate_bin", "scan", "bin_keys", "bin_scatter", "force")
+
+_NAMES = {ERR_ARG: "DPD_ERR_ARG", ERR_NOMEM: "DPD_ERR_NOMEM", ERR_CUDA: "DPD_ERR_CUDA",
+          ERR_STATE: "DPD_ERR_STATE", ERR_NUMERIC: "DPD_ERR_NUMERIC",
+          ERR_TIMEOUT: "DPD_ERR_TIMEOUT", ERR_BUSY: "DPD_ERR_BUSY"}
+
+
+class DPDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("momentum", ctypes.c_double * 3), ("kinetic", ctypes.c_double),
+                ("kT", ctypes.c_double), ("virial", ctypes.c_double),
+                ("pressure", ctypes.c_double), ("step", ctypes.c_int64), ("n", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {"momentum": np.array(self.momentum[:]), "kinetic": self.kinetic, "kT": self.kT,
+                "virial": self.virial, "pressure": self.pressure, "step": self.step, "n": self.n}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1911_04712_gb300.build` (there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    c = ctypes
+    vp, i64, u64, dbl, i32 = c.c_void_p, c.c_int64, c.c_uint64, c.c_double, c.c_int
+    L.dpd_last_error.restype = c.c_char_p
+    L.dpd_version.restype = c.c_char_p
+    L.dpd_create.argtypes = [c.POINTER(vp), c.POINTER(dbl), dbl, dbl, dbl, dbl, dbl, u64]
+    L.dpd_destroy.argtypes = [vp]
+    L.dpd_set_param.argtypes = [vp, i32, dbl]
+    L.dpd_set_stream.argtypes = [vp, vp]
+    L.dpd_set_state.argtypes = [vp, i64, vp, vp, i32]
+    L.dpd_step.argtypes = [vp, i64]
+    L.dpd_get_state.argtypes = [vp, vp, vp, i32]
+    L.dpd_get_forces.argtypes = [vp, vp, i32]
+    L.dpd_get_stats.argtypes = [vp, c.POINTER(Stats)]
+    L.dpd_num_particles.argtypes = [vp]
+    L.dpd_num_particles.restype = i64
+    L.dpd_profile_steps.argtypes = [vp, i64, c.POINTER(dbl)]
+    L.dpd_profile_steps.restype = i32
+    L.dpd_debug_rng.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp]
+    for name in ("dpd_create", "dpd_destroy", "dpd_set_param", "dpd_set_stream", "dpd_set_state",
+                 "dpd_step", "dpd_get_state", "dpd_get_forces", "dpd_get_stats",
+                 "dpd_debug_rng"):
+        getattr(L, name).restype = i32
+    _register_batch(L)
+    _lib = L
+    return L
+
+
+def _register_batch(L):
+    """Declare the multi-box and queue entry points when the library has them."""
+    try:
+        from . import batch as _b
+    except ImportError:  # pragma: no cover
+        return
+    _b.declare(L)
+
+
+def check(rc: int):
+    if rc != OK:
+        raise DPDError(rc, lib().dpd_last_error().decode(errors="replace"))
+    return rc
+
+
+def version() -> str:
+    return lib().dpd_version().decode()
+
+
+# ----------------------------------------------------------------- helpers
+def _is_cuda_tensor(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def _vec3_arg(x, n=None):
+    """(pointer, where, keepalive) for an n x 3 float32 array or CUDA tensor."""
+    if _is_cuda_tensor(x):
+        import torch
+        t = x.detach()
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            t = t.to(torch.float32).contiguous()
+        if t.dim() != 2 or t.shape[1] != 3 or (n is not None and t.shape[0] != n):
+            raise ValueError("expected an n x 3 tensor")
+        return ctypes.c_void_p(t.data_ptr()), WHERE_DEVICE, t
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 3 or (n is not None and a.shape[0] != n):
+        raise ValueError("expected an n x 3 array")
+    return a.ctypes.data_as(ctypes.c_void_p), WHERE_HOST, a
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# --------------------------------------------------------------------- box
+class Box:
+    """One periodic DPD box behind the dpd_* C ABI."""
+
+    def __init__(self, L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, *,
+                 stencil=None, kexp=None, mass=None, body_force=None, poiseuille_f=None,
+                 flow_axis=None, grad_axis=None, stream=None):
+        L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+        self.L = tuple(float(v) for v in L3)
+        self._ctx = ctypes.c_void_p()
+        box = (ctypes.c_double * 3)(*self.L)
+        check(lib().dpd_create(ctypes.byref(self._ctx), box, a, gamma, kT, rc, dt, int(seed)))
+        self.n = 0
+        for key, val in ((PARAM_FLOW_AXIS, flow_axis), (PARAM_GRAD_AXIS, grad_axis),
+                         (PARAM_KEXP, kexp), (PARAM_MASS, mass), (PARAM_BODYFORCE, body_force),
+                         (PARAM_POISEUILLE_F, poiseuille_f), (PARAM_STENCIL, stencil)):
+            if val is not None:
+                self.set_param(key, val)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().dpd_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_param(self, key: int, value: float):
+        check(lib().dpd_set_param(self._ctx, int(key), float(value)))
+
+    def set_stream(self, stream):
+        check(lib().dpd_set_stream(self._ctx, _stream_ptr(stream)))
+        self._stream_ref = stream   # the stream must outlive the work enqueued on it
+
+    def set_state(self, pos, vel):
+        n = int(pos.shape[0])
+        pp, wp, kp = _vec3_arg(pos, n)
+        vv, wv, kv = _vec3_arg(vel, n)
+        if wp != wv:
+            raise ValueError("pos and vel must both be host arrays or both CUDA tensors")
+        check(lib().dpd_set_state(self._ctx, n, pp, vv, wp))
+        self.n = n
+
+    def step(self, nsteps: int = 1):
+        check(lib().dpd_step(self._ctx, int(nsteps)))
+
+    def get_state(self, device: bool = False):
+        """(positions, full-step velocities) in id order: NumPy, or CUDA tensors if device."""
+        if device:
+            import torch
+            pos = torch.empty((self.n, 3), dtype=torch.float32, device="cuda")
+            vel = torch.empty_like(pos)
+            check(lib().dpd_get_state(self._ctx, ctypes.c_void_p(pos.data_ptr()),
+                                      ctypes.c_void_p(vel.data_ptr()), WHERE_DEVICE))
+            return pos, vel
+        pos = np.empty((self.n, 3), dtype=np.float32)
+        vel = np.empty_like(pos)
+        check(lib().dpd_get_state(self._ctx, pos.ctypes.data_as(ctypes.c_void_p),
+                                  vel.ctypes.data_as(ctypes.c_void_p), WHERE_HOST))
+        return pos, vel
+
+    def get_state_into(self, pos, vel):
+        """Fill caller-provided n x 3 buffers (pinned host tensors/arrays or CUDA tensors)."""
+        pp, wp, _ = _vec3_arg(pos, self.n) if not _is_cuda_tensor(pos) else (
+            ctypes.c_void_p(pos.data_ptr()), WHERE_DEVICE, pos)
+        vv, _, _ = _vec3_arg(vel, self.n) if not _is_cuda_tensor(vel) else (
+            ctypes.c_void_p(vel.data_ptr()), WHERE_DEVICE, vel)
+        check(lib().dpd_get_state(self._ctx, pp, vv, wp))
+
+    def get_forces(self, device: bool = False):
+        if device:
+            import torch
+            f = torch.empty((self.n, 3), dtype=torch.float32, device="cuda")
+            check(lib().dpd_get_forces(self._ctx, ctypes.c_void_p(f.data_ptr()), WHERE_DEVICE))
+            return f
+        f = np.empty((self.n, 3), dtype=np.float32)
+        check(lib().dpd_get_forces(self._ctx, f.ctypes.data_as(ctypes.c_void_p), WHERE_HOST))
+        return f
+
+    def profile(self, nsteps: int) -> list:
+        """Mean device ms per stage over nsteps steps: [integrate+count, scan,
+        key pass, reorder, force]."""
+        ms = (ctypes.c_double * NUM_STAGES)()
+        check(lib().dpd_profile_steps(self._ctx, int(nsteps), ms))
+        return list(ms)
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(lib().dpd_get_stats(self._ctx, ctypes.byref(s)))
+        return s.as_dict()
+
+
+def debug_rng(lo, hi, step: int, seed: int, stream=None):
+    """Noise words (uint32) and FP32 xi for pairs (lo[k], hi[k]) computed on the GPU."""
+    import torch
+    lo = np.ascontiguousarray(lo, dtype=np.uint32)
+    hi = np.ascontiguousarray(hi, dtype=np.uint32)
+    n = lo.size
+    d_lo = torch.from_numpy(lo.view(np.int32)).cuda()
+    d_hi = torch.from_numpy(hi.view(np.int32)).cuda()
+    d_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_xi = torch.empty(n, dtype=torch.float32, device="cuda")
+    check(lib().dpd_debug_rng(ctypes.c_void_p(d_lo.data_ptr()), ctypes.c_void_p(d_hi.data_ptr()),
+                              n, int(step), int(seed), ctypes.c_void_p(d_out.data_ptr()),
+                              ctypes.c_void_p(d_xi.data_ptr()), _stream_ptr(stream)))
+    return d_out.cpu().numpy().view(np.uint32), d_xi.cpu().numpy()

@@ -1,0 +1,312 @@
+"""GPU path against the FP64 oracle, through the C ABI.
+
+Tolerances (fixed by the contract of the method's FP32 implementation):
+* noise words bit-exact; FP32 xi within 1 ulp of the FP64 value;
+* per-particle forces from an identical state within 1e-5 of the force RMS;
+* 100-step trajectories within 1e-3 rc (minimum image, matched by id);
+* total momentum within 1e-6 of the summed momentum magnitude sum_i m |v_i|.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_04712_gb300.workloads import uniform_box_state
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+TRAJ_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def dpd():
+    from paper_1911_04712_gb300 import build
+    build.build()
+    import paper_1911_04712_gb300.dpd as d
+    return d
+
+
+def _params(L, seed=0, **kw):
+    L3 = tuple(np.broadcast_to(np.asarray(L, float), (3,)))
+    base = dict(a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005)
+    base.update(kw)
+    return O.Params(L=L3, seed=seed, **base)
+
+
+def _box(dpd, p: O.Params, stencil=0):
+    box = dpd.Box(p.L, a=p.a, gamma=p.gamma, kT=p.kT, rc=p.rc, dt=p.dt, seed=p.seed,
+                  stencil=stencil, kexp=p.kexp, mass=p.mass)
+    if p.fb_mode:
+        box.set_param(dpd.PARAM_FLOW_AXIS, p.fb_flow)
+        box.set_param(dpd.PARAM_GRAD_AXIS, p.fb_grad)
+        box.set_param(dpd.PARAM_BODYFORCE if p.fb_mode == O.FB_CONST else dpd.PARAM_POISEUILLE_F,
+                      p.fb)
+    return box
+
+
+def _min_image(d, L):
+    L = np.asarray(L, float)
+    return d - L * np.round(d / L)
+
+
+def _force_check(f_gpu, f_ref):
+    rms = math.sqrt((f_ref ** 2).sum(1).mean())
+    err = np.abs(f_gpu.astype(np.float64) - f_ref).max()
+    assert err <= FORCE_TOL * rms, f"max force error {err:.3e} > {FORCE_TOL} x rms {rms:.3f}"
+    return err / rms
+
+
+# ---------------------------------------------------------------- noise
+def test_rng_words_bit_exact(dpd):
+    rng = np.random.default_rng(5)
+    n = 1 << 16
+    lo = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    hi = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    lo[:4] = [0, 0xFFFFFFFF, 7, 7]
+    hi[:4] = [0, 0xFFFFFFFF, 7, 3]
+    for step, seed in ((0, 0), (123456789012, 0xDEADBEEFCAFEF00D), (1, 2)):
+        words, xi = dpd.debug_rng(lo, hi, step, seed)
+        ref_w, ref_xi = O.pair_rng(lo, hi, step, seed)
+        assert np.array_equal(words, ref_w)
+        ulp = np.spacing(np.abs(ref_xi).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(xi.astype(np.float64) - ref_xi) <= ulp)
+
+
+# ---------------------------------------------------------------- forces
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_forces_identical_state_L8(dpd, stencil):
+    x, v = uniform_box_state(8, rho=3, seed=0)
+    p = _params(8, seed=0)
+    box = _box(dpd, p, stencil)
+    box.set_state(x, v)
+    f_ref, vir = O.forces(p, x, v, 0)
+    _force_check(box.get_forces(), f_ref)
+    st = box.stats()
+    assert st["virial"] == pytest.approx(vir, rel=1e-5)
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("L,rho,n", [
+    ((5.0, 6.5, 7.25), 3, None),     # non-integer edges, ragged count
+    (3.0, 5, None),                  # minimum box: 3 cells per axis
+    ((3.0, 11.0, 4.0), 4, None),     # thin box
+    (6.0, 3, 1),                     # one particle
+    (6.0, 3, 2),                     # one pair
+    (4.0, 3, 4000),                  # dense: ~62 per cell, lists drain often
+])
+def test_forces_ragged_and_edge_boxes(dpd, stencil, L, rho, n):
+    x, v = uniform_box_state(L, rho=rho, n=n, seed=3)
+    if n == 2:
+        x[1] = x[0] + np.float32(0.5)
+        x[1] = np.mod(x[1], np.float32(L))
+    p = _params(L, seed=9)
+    box = _box(dpd, p, stencil)
+    box.set_state(x, v)
+    f_ref, _ = O.forces(p, x, v, 0)
+    if x.shape[0] >= 2:
+        _force_check(box.get_forces(), f_ref)
+    else:
+        assert np.all(box.get_forces() == 0)
+
+
+def test_particles_on_cell_and_box_faces(dpd):
+    L = 6.0
+    x, v = uniform_box_state(L, rho=3, seed=4)
+    rng = np.random.default_rng(4)
+    idx = rng.choice(len(x), 200, replace=False)
+    faces = rng.integers(0, 6, (200, 3)).astype(np.float32)
+    x[idx] = np.where(rng.random((200, 3)) < 0.5, faces, x[idx])
+    x[idx[:20], 0] = np.float32(np.nextafter(np.float32(L), np.float32(0)))
+    p = _params(L, seed=4)
+    box = _box(dpd, p)
+    box.set_state(x, v)
+    f_ref, _ = O.forces(p, x, v, 0)
+    _force_check(box.get_forces(), f_ref)
+
+
+def test_positions_outside_box_are_wrapped(dpd):
+    L = 5.0
+    x, v = uniform_box_state(L, rho=3, seed=6)
+    shifted = x + np.float32(L) * np.random.default_rng(6).integers(-2, 3, x.shape).astype(np.float32)
+    p = _params(L, seed=6)
+    box = _box(dpd, p)
+    box.set_state(shifted, v)
+    xg, _ = box.get_state()
+    d = _min_image(xg.astype(np.float64) - x, L)
+    assert np.abs(d).max() < 1e-5
+    assert np.all(xg >= 0) and np.all(xg < L)
+
+
+def test_body_forces_match_oracle(dpd):
+    x, v = uniform_box_state(6, rho=3, seed=7)
+    for mode, flow, grad in ((O.FB_CONST, 0, 1), (O.FB_POISEUILLE, 2, 0), (O.FB_POISEUILLE, 0, 1)):
+        p = _params(6, seed=7, fb=0.5, fb_mode=mode, fb_flow=flow, fb_grad=grad)
+        box = _box(dpd, p)
+        box.set_state(x, v)
+        f_ref, _ = O.forces(p, x, v, 0)
+        _force_check(box.get_forces(), f_ref)
+
+
+def test_weight_exponent_and_mass(dpd):
+    x, v = uniform_box_state(6, rho=4, seed=8)
+    p = _params(6, seed=8, kexp=0.5, mass=2.0)
+    box = _box(dpd, p)
+    box.set_state(x, v)
+    f_ref, _ = O.forces(p, x, v, 0)
+    _force_check(box.get_forces(), f_ref)
+    box.step(30)
+    s = O.State(p, x, v)
+    s.run(30)
+    xg, vg = box.get_state()
+    assert np.abs(_min_image(xg - s.x, 6.0)).max() < TRAJ_TOL
+
+
+# ---------------------------------------------------------- trajectories
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_trajectory_100_steps_L8(dpd, stencil):
+    L = 8.0
+    x, v = uniform_box_state(L, rho=3, seed=0)
+    p = _params(L, seed=0)
+    box = _box(dpd, p, stencil)
+    box.set_state(x, v)
+    box.step(100)
+    xg, vg = box.get_state()
+    s = O.State(p, x, v)
+    s.run(100)
+    dx = np.abs(_min_image(xg.astype(np.float64) - s.x, L)).max()
+    dv = np.abs(vg.astype(np.float64) - s.v).max()
+    assert dx < TRAJ_TOL, dx
+    assert dv < 0.05, dv
+    # momentum: |P(t) - P(0)| within 1e-6 of sum_i m |v_i|
+    P0 = v.astype(np.float64).sum(0)
+    st = box.stats()
+    scale = np.linalg.norm(vg.astype(np.float64), axis=1).sum()
+    assert np.abs(st["momentum"] - P0).max() <= 1e-6 * scale
+    assert st["step"] == 100
+    ref = s.stats()
+    assert st["kT"] == pytest.approx(ref["kT"], rel=1e-3)
+    assert st["pressure"] == pytest.approx(ref["pressure"], rel=1e-3)
+
+
+def test_constant_body_force_momentum(dpd):
+    L, f0, nst = 6.0, 0.05, 64
+    x, v = uniform_box_state(L, rho=3, seed=2)
+    p = _params(L, seed=2, fb=f0, fb_mode=O.FB_CONST, fb_flow=0)
+    box = _box(dpd, p)
+    box.set_state(x, v)
+    P0 = box.stats()["momentum"]
+    box.step(nst)
+    _, vg = box.get_state()
+    P = box.stats()["momentum"]
+    scale = np.linalg.norm(vg.astype(np.float64), axis=1).sum()
+    want = np.array([len(x) * f0 * nst * p.dt, 0.0, 0.0])
+    assert np.abs(P - P0 - want).max() <= 1e-6 * scale
+
+
+def test_free_streaming(dpd):
+    L = (5.0, 6.0, 7.0)
+    x, v = uniform_box_state(L, rho=3, seed=3)
+    p = _params(L, a=0.0, gamma=0.0, kT=0.0)
+    box = _box(dpd, p)
+    box.set_state(x, v)
+    box.step(100)
+    xg, vg = box.get_state()
+    want = np.mod(x.astype(np.float64) + 100 * 0.005 * v.astype(np.float64), np.asarray(L))
+    assert np.abs(_min_image(xg - want, L)).max() < 1e-4
+    assert np.array_equal(vg, v)
+
+
+def test_empty_box(dpd):
+    box = _box(dpd, _params(5.0))
+    box.set_state(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+    box.step(10)
+    xg, vg = box.get_state()
+    assert xg.shape == (0, 3)
+    assert box.stats()["step"] == 10
+
+
+# ------------------------------------------------------- reproducibility
+def test_full_stencil_is_bitwise_reproducible_and_graph_equals_direct(dpd):
+    L = 8.0
+    x, v = uniform_box_state(L, rho=3, seed=1)
+    p = _params(L, seed=1)
+    outs = []
+    for chunks in ((40,), (1,) * 40, (33, 7)):
+        box = _box(dpd, p)
+        box.set_state(x, v)
+        for c in chunks:
+            box.step(c)
+        outs.append(box.get_state())
+    for xg, vg in outs[1:]:
+        assert np.array_equal(xg, outs[0][0]) and np.array_equal(vg, outs[0][1])
+
+
+def test_device_pointer_io_matches_host(dpd):
+    import torch
+    L = 6.0
+    x, v = uniform_box_state(L, rho=3, seed=5)
+    p = _params(L, seed=5)
+    b1 = _box(dpd, p)
+    b1.set_state(x, v)
+    b2 = _box(dpd, p)
+    b2.set_state(torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda())
+    b1.step(10)
+    b2.step(10)
+    xh, vh = b1.get_state()
+    xd, vd = b2.get_state(device=True)
+    assert np.array_equal(xh, xd.cpu().numpy()) and np.array_equal(vh, vd.cpu().numpy())
+    assert np.array_equal(b1.get_forces(), b2.get_forces(device=True).cpu().numpy())
+
+
+def test_user_stream(dpd):
+    import torch
+    L = 6.0
+    x, v = uniform_box_state(L, rho=3, seed=5)
+    p = _params(L, seed=5)
+    s = torch.cuda.Stream()
+    b1 = _box(dpd, p)
+    b1.set_stream(s)
+    b1.set_state(x, v)
+    b1.step(40)
+    b2 = _box(dpd, p)
+    b2.set_state(x, v)
+    b2.step(40)
+    assert np.array_equal(b1.get_state()[0], b2.get_state()[0])
+
+
+def test_non_finite_input_is_reported(dpd):
+    L = 5.0
+    x, v = uniform_box_state(L, rho=3, seed=1)
+    v[3, 1] = np.nan
+    box = _box(dpd, _params(L))
+    box.set_state(x, v)
+    box.step(2)
+    with pytest.raises(dpd.DPDError) as ei:
+        box.get_state()
+    assert ei.value.code == dpd.ERR_NUMERIC
+
+
+# -------------------------------------------------- full-size sampled parity
+@pytest.mark.parametrize("L", [64.0, 128.0])
+def test_full_size_forces_sampled(dpd, L):
+    x, v = uniform_box_state(L, rho=3, seed=0)
+    p = _params(L, seed=0)
+    box = _box(dpd, p)
+    box.set_state(x, v)
+    box.step(3)                         # exercise binning at full size
+    xg, vg = box.get_state()
+    box2 = _box(dpd, p)
+    box2.set_state(xg, vg)
+    fg = box2.get_forces()
+    which = np.random.default_rng(1).choice(len(x), 1500, replace=False)
+    f_ref = O.forces_subset(p, xg, vg, which, 0)
+    rms = math.sqrt((f_ref ** 2).sum(1).mean())
+    err = np.abs(fg[which].astype(np.float64) - f_ref).max()
+    assert err <= FORCE_TOL * rms, (err, rms)
+    # properties at full size: zero net pair force, ids intact, positions in box
+    ssum = np.abs(fg.astype(np.float64).sum(0)).max()
+    assert ssum <= 1e-6 * np.abs(fg).sum()
+    assert np.all(xg >= 0) and np.all(xg < L)
