@@ -209,8 +209,9 @@ def run_native(args):
     x, v = uniform_box_state(L, rho=rho, seed=args.seed + rank)
     n = x.shape[0]
     stream = torch.cuda.current_stream()
+    tiling = dict(tiles=args.tiles, tile_cells=args.tile_cells, stage_cap=args.stage_cap)
     box = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed + rank,
-                  stencil=(1 if args.stencil == "half" else 0), stream=stream)
+                  stencil=(1 if args.stencil == "half" else 0), stream=stream, **tiling)
     box.set_state(x, v)
     box.step(args.warmup)
     torch.cuda.synchronize()
@@ -268,7 +269,7 @@ def run_native(args):
         hp.numpy()[:] = x
         hv.numpy()[:] = v
         ebox = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed + rank,
-                       stencil=(1 if args.stencil == "half" else 0), stream=stream)
+                       stencil=(1 if args.stencil == "half" else 0), stream=stream, **tiling)
         ebox.set_state(hp.numpy(), hv.numpy())      # warm allocation
         ebox.step(2)
         ebox.stats()
@@ -304,7 +305,8 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"dpd_periodic_box_L{L:g}_rho{rho:g}", "particles": n,
                        "L": L, "rho": rho, "a": 25.0, "gamma": 4.5, "kT": 1.0, "dt": 0.005,
-                       "stencil": args.stencil, "l2": "state larger than L2 "
+                       "stencil": args.stencil, "force_tiles": box.tiling(),
+                       "l2": "state larger than L2 "
                        f"({48 * n / 1e6:.0f} MB of float4 x, v, f)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "kernel": "force", "achieved": achieved,
@@ -336,6 +338,9 @@ def main():
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--stencil", choices=("full", "half"), default="full")
+    ap.add_argument("--tiles", type=int, default=None, help="1: staged force tiles, 0: direct")
+    ap.add_argument("--tile-cells", type=int, default=None)
+    ap.add_argument("--stage-cap", type=int, default=None)
     ap.add_argument("--cpu-L", type=float, default=64.0)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-L", type=float, default=32.0)

@@ -85,6 +85,13 @@ typedef struct dpd_ctx dpd_ctx;
 #define DPD_PARAM_GRAD_AXIS 6     /* 0, 1, 2: axis the Poiseuille force switches on; default 0 (x) */
 #define DPD_PARAM_STENCIL 7       /* DPD_STENCIL_FULL (default) or DPD_STENCIL_HALF */
 
+#define DPD_PARAM_FORCE_TILES 8   /* full stencil: 1 stages each block's neighbourhood in shared
+                                     memory; 0 (default) has one thread per particle read its
+                                     neighbours through the L1 cache (faster on GB300) */
+#define DPD_PARAM_TILE_CELLS 9    /* cells per staged tile, 1..64; 0 (default) = chosen by density */
+#define DPD_PARAM_STAGE_CAP 10    /* staged particles per block, 64..4096; 0 (default) = by density;
+                                     blocks whose neighbourhood exceeds it read global memory */
+
 #define DPD_STENCIL_FULL 0  /* 27 cells, each thread sums its own pairs: no atomics,
                                bitwise reproducible */
 #define DPD_STENCIL_HALF 1  /* 13 cells + own cell, Newton's third law with atomics
@@ -105,6 +112,11 @@ DPD_API int dpd_destroy(dpd_ctx *ctx);
 /* Set one DPD_PARAM_* value.  Takes effect at the next dpd_set_state or
  * dpd_step.  Errors: DPD_ERR_ARG for an unknown key or bad value. */
 DPD_API int dpd_set_param(dpd_ctx *ctx, int key, double value);
+
+/* Read one DPD_PARAM_* value.  For DPD_PARAM_TILE_CELLS and
+ * DPD_PARAM_STAGE_CAP the value in use is returned (after dpd_set_state,
+ * the one chosen by density when the parameter was left at 0). */
+DPD_API int dpd_get_param(const dpd_ctx *ctx, int key, double *value);
 
 /* Enqueue all later work of the context on the given cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream).  NULL = legacy default stream. */

@@ -18,6 +18,7 @@ struct dpd_ctx {
   BoxParams bp{};
   int64_t n = 0;
   bool loaded = false;
+  int tiles = 0, tile_cells = 0, stage_cap = 0;
 };
 
 extern "C" {
@@ -93,6 +94,22 @@ int dpd_set_param(dpd_ctx *ctx, int key, double value) {
       if (!(value == DPD_STENCIL_FULL || value == DPD_STENCIL_HALF))
         return dpd::set_error(DPD_ERR_ARG, "stencil must be DPD_STENCIL_FULL or DPD_STENCIL_HALF");
       return ctx->eng.set_stencil((int)value);
+    case DPD_PARAM_FORCE_TILES:
+    case DPD_PARAM_TILE_CELLS:
+    case DPD_PARAM_STAGE_CAP: {
+      if (!(value >= 0.0 && value <= 1e6) || value != (double)(int)value)
+        return dpd::set_error(DPD_ERR_ARG, "tiling parameters are non-negative integers");
+      int t = ctx->tiles, c = ctx->tile_cells, cap = ctx->stage_cap;
+      if (key == DPD_PARAM_FORCE_TILES) t = (value != 0.0);
+      if (key == DPD_PARAM_TILE_CELLS) c = (int)value;
+      if (key == DPD_PARAM_STAGE_CAP) cap = (int)value;
+      rc = ctx->eng.set_tiling(t, c, cap);
+      if (rc) return rc;
+      ctx->tiles = t;
+      ctx->tile_cells = c;
+      ctx->stage_cap = cap;
+      return DPD_OK;
+    }
     default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
   }
   if (rc) return rc;
@@ -101,6 +118,27 @@ int dpd_set_param(dpd_ctx *ctx, int key, double value) {
   if (rc) return rc;
   ctx->bp = bp;
   if (ctx->loaded) return ctx->eng.update_params({bp});
+  return DPD_OK;
+}
+
+int dpd_get_param(const dpd_ctx *ctx, int key, double *value) {
+  dpd::clear_error();
+  if (!ctx || !value) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  const BoxParams &bp = ctx->bp;
+  const dpd::StepConfig &cfg = ctx->eng.step_config();
+  switch (key) {
+    case DPD_PARAM_KEXP: *value = bp.kexp; break;
+    case DPD_PARAM_MASS: *value = bp.mass; break;
+    case DPD_PARAM_BODYFORCE: *value = bp.fb_mode == 1 ? bp.fb : 0.0; break;
+    case DPD_PARAM_POISEUILLE_F: *value = bp.fb_mode == 2 ? bp.fb : 0.0; break;
+    case DPD_PARAM_FLOW_AXIS: *value = bp.fb_flow; break;
+    case DPD_PARAM_GRAD_AXIS: *value = bp.fb_grad; break;
+    case DPD_PARAM_STENCIL: *value = cfg.stencil; break;
+    case DPD_PARAM_FORCE_TILES: *value = cfg.tiles ? 1.0 : 0.0; break;
+    case DPD_PARAM_TILE_CELLS: *value = ctx->loaded ? cfg.grid.tc : ctx->tile_cells; break;
+    case DPD_PARAM_STAGE_CAP: *value = ctx->loaded ? cfg.grid.stage_cap : ctx->stage_cap; break;
+    default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
+  }
   return DPD_OK;
 }
 

@@ -101,6 +101,7 @@ Engine::~Engine() {
     drop_graph();
     free_all();
     if (d_.err) cudaFree(d_.err);
+    if (d_tiles_) cudaFree(d_tiles_);
     if (cap_) cudaStreamDestroy(cap_);
     if (cur >= 0 && cur != device_) cudaSetDevice(cur);
   }
@@ -135,9 +136,81 @@ int Engine::set_stream(cudaStream_t s) {
 
 int Engine::set_stencil(int stencil) {
   if (stencil != 0 && stencil != 1) return set_error(DPD_ERR_ARG, "stencil must be 0 or 1");
-  if (stencil != stencil_) {
-    stencil_ = stencil;
+  if (stencil != cfg_.stencil) {
+    cfg_.stencil = stencil;
     drop_graph();
+  }
+  return DPD_OK;
+}
+
+int Engine::set_tiling(int use_tiles, int tc, int stage_cap) {
+  if (tc < 0 || tc > kTileMaxCells) return set_error(DPD_ERR_ARG, "cells per tile must be 0..%d", kTileMaxCells);
+  if (stage_cap != 0 && (stage_cap < 64 || stage_cap > 4096))
+    return set_error(DPD_ERR_ARG, "staging capacity must be 0 or 64..4096 particles");
+  cfg_.tiles = use_tiles != 0;
+  tile_tc_override_ = tc;
+  stage_cap_override_ = stage_cap;
+  drop_graph();
+  if (!boxes_.empty()) return build_tiles();
+  return DPD_OK;
+}
+
+// Cells per tile and staging capacity by density: about 9 (tc + 2) rho
+// particles are staged; tc is chosen so that this stays near 900 (about
+// 100 targets per block of 128 threads).
+static int tile_cells_for(double rho, int nx) {
+  int tc = (int)std::lround(102.0 / std::max(rho, 0.5)) - 2;
+  tc = std::max(2, std::min(tc, kTileMaxCells));
+  return std::min(tc, nx);
+}
+
+int Engine::build_tiles() {
+  const int nb = nbox();
+  int stage_need = 0;
+  tiles_h_.clear();
+  int tc_single = 0;
+  for (int b = 0; b < nb; ++b) {
+    const BoxDev &B = boxes_[b];
+    const double V = (double)B.L[0] * B.L[1] * B.L[2];
+    const double rho = (double)B.np / V;
+    int tc = tile_tc_override_ > 0 ? std::min(tile_tc_override_, B.n[0]) : tile_cells_for(rho, B.n[0]);
+    const double h3 = V / ((double)B.n[0] * B.n[1] * B.n[2]);
+    const int need = (int)std::ceil(9.0 * (tc + 2) * rho * h3 * 1.35) + 64;
+    stage_need = std::max(stage_need, need);
+    if (b == 0) tc_single = tc;
+    if (nb > 1) {
+      const int tpr = (B.n[0] + tc - 1) / tc;
+      for (int cz = 0; cz < B.n[2]; ++cz)
+        for (int cy = 0; cy < B.n[1]; ++cy)
+          for (int t = 0; t < tpr; ++t) {
+            const int cx0 = t * tc;
+            const int nc = std::min(tc, B.n[0] - cx0);
+            tiles_h_.push_back(make_int4(b, cy, cz, cx0 | (nc << 16)));
+          }
+    }
+  }
+  int cap = stage_cap_override_ > 0 ? stage_cap_override_ : ((stage_need + 63) / 64) * 64;
+  cap = std::min(cap, 4096);
+  cfg_.grid.stage_cap = cap;
+  if (nb == 1) {
+    const BoxDev &B = boxes_[0];
+    cfg_.grid.list = nullptr;
+    cfg_.grid.tc = tc_single;
+    cfg_.grid.tpr = (B.n[0] + tc_single - 1) / tc_single;
+    cfg_.grid.ntiles = cfg_.grid.tpr * B.n[1] * B.n[2];
+  } else {
+    if (tiles_h_.size() > cap_tiles_) {
+      if (d_tiles_) cudaFree(d_tiles_);
+      d_tiles_ = nullptr;
+      DPD_CUDA_TRY(cudaMalloc(&d_tiles_, tiles_h_.size() * sizeof(int4)));
+      cap_tiles_ = tiles_h_.size();
+    }
+    DPD_CUDA_TRY(cudaMemcpyAsync(d_tiles_, tiles_h_.data(), tiles_h_.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, stream_));
+    cfg_.grid.list = d_tiles_;
+    cfg_.grid.tc = 0;
+    cfg_.grid.tpr = 0;
+    cfg_.grid.ntiles = (int)tiles_h_.size();
   }
   return DPD_OK;
 }
@@ -252,7 +325,7 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
     boxes[b] = make_box_dev(params[b], (int)ctot, (int)ptot, (int)np[b]);
     ptot += np[b];
     ctot += (int64_t)n[0] * n[1] * n[2];
-    if (ptot > (int64_t)(1 << 30) || ctot > (int64_t)(1 << 30))
+    if (ptot >= (int64_t)(1 << 26) || ctot > (int64_t)(1 << 30))
       return set_error(DPD_ERR_ARG, "packed set too large (%lld particles, %lld cells)",
                        (long long)ptot, (long long)ctot);
   }
@@ -271,7 +344,7 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
                                cudaMemcpyHostToDevice, stream_));
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.pbase, pbase_.data(), pbase_.size() * sizeof(int),
                                cudaMemcpyHostToDevice, stream_));
-  return DPD_OK;
+  return build_tiles();
 }
 
 int Engine::update_params(const std::vector<BoxParams> &params) {
@@ -328,7 +401,7 @@ int Engine::rebuild() {
   for (auto &s : st_host_) s.adv = 1;
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.st, st_host_.data(), st_host_.size() * sizeof(BoxState),
                                cudaMemcpyHostToDevice, stream_));
-  DPD_CUDA_TRY(launch_step(packed(), false, false, stencil_, stream_));
+  DPD_CUDA_TRY(launch_step(packed(), false, false, cfg_, stream_));
   return DPD_OK;
 }
 
@@ -339,7 +412,7 @@ int Engine::capture_graph() {
   DPD_CUDA_TRY(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < graph_chunk && e == cudaSuccess; ++k)
-    e = launch_step(P, true, true, stencil_, cap_);
+    e = launch_step(P, true, true, cfg_, cap_);
   cudaError_t e2 = cudaStreamEndCapture(cap_, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -383,7 +456,7 @@ int Engine::step(int64_t nsteps) {
     }
   }
   const Packed P = packed();
-  for (int64_t k = 0; k < left; ++k) DPD_CUDA_TRY(launch_step(P, true, true, stencil_, stream_));
+  for (int64_t k = 0; k < left; ++k) DPD_CUDA_TRY(launch_step(P, true, true, cfg_, stream_));
   for (auto &s : st_host_) {
     const int64_t k = std::min<int64_t>(s.remaining, nsteps);
     s.step += (unsigned long long)k;
@@ -401,7 +474,7 @@ int Engine::profile(int64_t nsteps, double *stage_ms) {
   const Packed P = packed();
   int rc = DPD_OK;
   for (int64_t s = 0; s < nsteps && rc == DPD_OK; ++s) {
-    cudaError_t e = launch_step_timed(P, stencil_, stream_, ev);
+    cudaError_t e = launch_step_timed(P, cfg_, stream_, ev);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[kNumStages]);
     if (e != cudaSuccess) {
       rc = set_error(DPD_ERR_CUDA, "profiled step: %s", cudaGetErrorString(e));

@@ -65,6 +65,11 @@ class Engine {
   int init();                       // binds the current device, prepares kernels
   int set_stream(cudaStream_t s);
   int set_stencil(int stencil);
+  // Force-kernel tiling: use_tiles = 0 selects one thread per particle reading
+  // neighbours from global memory; tc / stage_cap > 0 override the choice by
+  // density (cells per tile, staged particles per block).
+  int set_tiling(int use_tiles, int tc, int stage_cap);
+  const StepConfig &step_config() const { return cfg_; }
 
   // Lay out boxes: particle counts per box decide the slot ranges.  Allocates
   // (or grows) device memory and uploads descriptors.  Box state is reset.
@@ -114,7 +119,13 @@ class Engine {
   int device_ = -1;
   cudaStream_t stream_ = nullptr;   // caller's stream (nullptr: legacy default)
   cudaStream_t cap_ = nullptr;      // private stream used to capture graphs
-  int stencil_ = 0;
+  StepConfig cfg_{};
+  int tile_tc_override_ = 0;      // cells per tile forced by set_tiling (0: by density)
+  int stage_cap_override_ = 0;    // staging capacity forced by set_tiling (0: by density)
+  std::vector<int4> tiles_h_;
+  int4 *d_tiles_ = nullptr;
+  size_t cap_tiles_ = 0;
+  int build_tiles();
   std::vector<BoxParams> params_;
   std::vector<BoxDev> boxes_;
   std::vector<int> pbase_;

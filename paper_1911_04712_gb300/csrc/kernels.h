@@ -27,6 +27,27 @@ struct Packed {
   BoxDev single;
 };
 
+// Tiling of the staged force kernel.  Single box: tiles are computed from
+// the block index (tc cells per tile, tpr tiles per row).  Packed boxes:
+// `list` holds one int4 {box, cy, cz, cx0 | nc << 16} per tile.
+constexpr int kTileThreads = 128;
+constexpr int kTileMaxCells = 64;
+struct TileGrid {
+  const int4 *list;
+  int ntiles;
+  int tc;         // cells per tile
+  int tpr;        // tiles per row
+  int stage_cap;  // staged particles per block (positions + velocities)
+};
+
+// How a step is launched.
+struct StepConfig {
+  int stencil = 0;       // 0 full, 1 half
+  bool tiles = false;    // full stencil: staged tiles (true) or one thread per particle
+  TileGrid grid{};
+};
+size_t tile_smem_bytes(int stage_cap);
+
 struct StatsWork {  // one block of the statistics reduction
   int box, begin, end, pad;
 };
@@ -49,12 +70,14 @@ cudaError_t launch_load(const Packed &P, int box_slot0, int n, const float *pos3
 
 // One step (move = true) or the initial rebuild (move = false):
 // kick/drift/wrap + cell count, scan, reorder, force.
-cudaError_t launch_step(const Packed &P, bool move, bool advance, int stencil, cudaStream_t s);
+cudaError_t launch_step(const Packed &P, bool move, bool advance, const StepConfig &cfg,
+                        cudaStream_t s);
 
 // One step with events recorded around its stages: ev[0] before the
 // integrate/count kernel, then after it, after the scan, after the key pass,
 // after the reorder and after the force kernel (6 events).
-cudaError_t launch_step_timed(const Packed &P, int stencil, cudaStream_t s, cudaEvent_t *ev);
+cudaError_t launch_step_timed(const Packed &P, const StepConfig &cfg, cudaStream_t s,
+                              cudaEvent_t *ev);
 constexpr int kNumStages = 5;
 constexpr int kKernelsPerStep = 7;
 

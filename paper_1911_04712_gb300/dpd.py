@@ -22,6 +22,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_STATE, ERR_NUMERIC, ERR_TIMEOUT, ERR_BUSY 
 WHERE_HOST, WHERE_DEVICE = 0, 1
 PARAM_KEXP, PARAM_MASS, PARAM_BODYFORCE, PARAM_POISEUILLE_F = 1, 2, 3, 4
 PARAM_FLOW_AXIS, PARAM_GRAD_AXIS, PARAM_STENCIL = 5, 6, 7
+PARAM_FORCE_TILES, PARAM_TILE_CELLS, PARAM_STAGE_CAP = 8, 9, 10
 STENCIL_FULL, STENCIL_HALF = 0, 1
 NUM_STAGES, KERNELS_PER_STEP = 5, 7
 STAGE_NAMES = ("integrate_bin", "scan", "bin_keys", "bin_scatter", "force")
@@ -67,6 +68,8 @@ def lib():
     L.dpd_destroy.argtypes = [vp]
     L.dpd_set_param.argtypes = [vp, i32, dbl]
     L.dpd_set_stream.argtypes = [vp, vp]
+    L.dpd_get_param.argtypes = [vp, i32, c.POINTER(dbl)]
+    L.dpd_get_param.restype = i32
     L.dpd_set_state.argtypes = [vp, i64, vp, vp, i32]
     L.dpd_step.argtypes = [vp, i64]
     L.dpd_get_state.argtypes = [vp, vp, vp, i32]
@@ -140,7 +143,8 @@ class Box:
 
     def __init__(self, L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, *,
                  stencil=None, kexp=None, mass=None, body_force=None, poiseuille_f=None,
-                 flow_axis=None, grad_axis=None, stream=None):
+                 flow_axis=None, grad_axis=None, stream=None, tiles=None, tile_cells=None,
+                 stage_cap=None):
         L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
         self.L = tuple(float(v) for v in L3)
         self._ctx = ctypes.c_void_p()
@@ -149,7 +153,9 @@ class Box:
         self.n = 0
         for key, val in ((PARAM_FLOW_AXIS, flow_axis), (PARAM_GRAD_AXIS, grad_axis),
                          (PARAM_KEXP, kexp), (PARAM_MASS, mass), (PARAM_BODYFORCE, body_force),
-                         (PARAM_POISEUILLE_F, poiseuille_f), (PARAM_STENCIL, stencil)):
+                         (PARAM_POISEUILLE_F, poiseuille_f), (PARAM_STENCIL, stencil),
+                         (PARAM_FORCE_TILES, tiles), (PARAM_TILE_CELLS, tile_cells),
+                         (PARAM_STAGE_CAP, stage_cap)):
             if val is not None:
                 self.set_param(key, val)
         if stream is not None:
@@ -174,6 +180,17 @@ class Box:
 
     def set_param(self, key: int, value: float):
         check(lib().dpd_set_param(self._ctx, int(key), float(value)))
+
+    def get_param(self, key: int) -> float:
+        v = ctypes.c_double()
+        check(lib().dpd_get_param(self._ctx, int(key), ctypes.byref(v)))
+        return v.value
+
+    def tiling(self) -> dict:
+        """Force-kernel tiling in use: staged tiles on/off, cells per tile, staging capacity."""
+        return {"tiles": int(self.get_param(PARAM_FORCE_TILES)),
+                "tile_cells": int(self.get_param(PARAM_TILE_CELLS)),
+                "stage_cap": int(self.get_param(PARAM_STAGE_CAP))}
 
     def set_stream(self, stream):
         check(lib().dpd_set_stream(self._ctx, _stream_ptr(stream)))

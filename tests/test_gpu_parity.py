@@ -310,3 +310,34 @@ def test_full_size_forces_sampled(dpd, L):
     ssum = np.abs(fg.astype(np.float64).sum(0)).max()
     assert ssum <= 1e-6 * np.abs(fg).sum()
     assert np.all(xg >= 0) and np.all(xg < L)
+
+
+@pytest.mark.parametrize("tiling", [dict(tiles=0), dict(tiles=1), dict(tiles=1, tile_cells=1),
+                                    dict(tiles=1, tile_cells=3), dict(tiles=1, tile_cells=5),
+                                    dict(tiles=1, tile_cells=64),
+                                    dict(tiles=1, stage_cap=64)])  # 64: blocks overflow -> global path
+def test_force_tiling_variants(dpd, tiling):
+    for L, rho in (((5.0, 6.5, 7.25), 3), (3.0, 5), (8.0, 3), (4.0, 10)):
+        x, v = uniform_box_state(L, rho=rho, seed=11)
+        p = _params(L, seed=11)
+        box = dpd.Box(p.L, a=p.a, gamma=p.gamma, kT=p.kT, rc=p.rc, dt=p.dt, seed=p.seed, **tiling)
+        box.set_state(x, v)
+        f_ref, vir = O.forces(p, x, v, 0)
+        _force_check(box.get_forces(), f_ref)
+        assert box.stats()["virial"] == pytest.approx(vir, rel=1e-5)
+        box.step(5)
+        xg, vg = box.get_state()
+        b2 = dpd.Box(p.L, a=p.a, gamma=p.gamma, kT=p.kT, rc=p.rc, dt=p.dt, seed=p.seed, tiles=0)
+        b2.set_state(x, v)
+        b2.step(5)
+        x2, _ = b2.get_state()
+        assert np.abs(_min_image(xg.astype(np.float64) - x2, L)).max() < 1e-4
+
+
+def test_tiling_knobs_reported(dpd):
+    box = dpd.Box(8.0, tiles=1, tile_cells=5, stage_cap=512)
+    x, v = uniform_box_state(8.0, rho=3, seed=0)
+    box.set_state(x, v)
+    assert box.tiling() == {"tiles": 1, "tile_cells": 5, "stage_cap": 512}
+    with pytest.raises(dpd.DPDError):
+        box.set_param(dpd.PARAM_STAGE_CAP, 10)
