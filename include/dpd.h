@@ -176,6 +176,35 @@ DPD_API int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms);
 DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uint64_t step, uint64_t seed,
                   uint32_t *out, float *xi, void *stream);
 
+/* ------------------------------------------------- forces without allocation */
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory where they need forces (code inside a host
+ * callback or a custom allocator, a framework that has given all device
+ * memory to its own pool, a real-time loop that must not meet cudaMalloc's
+ * implicit device synchronisation).
+ *
+ * Pair forces plus nothing else (no body force, k = 1, m = 1) on n particles
+ * of one periodic box, at noise step `step`, from a caller-provided state.
+ * pos, vel: n x 3 FP32 DEVICE pointers (particle i has id i); force: n x 3
+ * FP32 DEVICE output, in the same order.  The result equals what
+ * dpd_set_state + dpd_get_forces gives for the same state at step 0.
+ *
+ * Allocates nothing: the scratch (about 3.3 MB) is one static device array
+ * of the library, held by every GPU that loads it until the process exits.
+ * Limits: n <= DPD_NOALLOC_MAX_PARTICLES and at most DPD_NOALLOC_MAX_CELLS
+ * cells (floor(L_d / rc) multiplied over the three axes); larger inputs
+ * return DPD_ERR_ARG.  The first call on each device looks the scratch up
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Work is enqueued on `stream` (NULL = legacy default) and the
+ * call returns without synchronising.  All calls share the one scratch
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+#define DPD_NOALLOC_MAX_PARTICLES 32768
+#define DPD_NOALLOC_MAX_CELLS 32767
+DPD_API int dpd_forces_noalloc(int64_t n, const float *pos, const float *vel, const double box[3],
+                               double a, double gamma, double kT, double rc, double dt,
+                               uint64_t seed, uint64_t step, float *force, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,9 @@ def lib():
     L.dpd_profile_steps.argtypes = [vp, i64, c.POINTER(dbl)]
     L.dpd_profile_steps.restype = i32
     L.dpd_debug_rng.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp]
+    L.dpd_forces_noalloc.argtypes = [i64, vp, vp, c.POINTER(dbl), dbl, dbl, dbl, dbl, dbl, u64,
+                                     u64, vp, vp]
+    L.dpd_forces_noalloc.restype = i32
     for name in ("dpd_create", "dpd_destroy", "dpd_set_param", "dpd_set_stream", "dpd_set_state",
                  "dpd_step", "dpd_get_state", "dpd_get_forces", "dpd_get_stats",
                  "dpd_debug_rng"):
@@ -268,3 +271,29 @@ def debug_rng(lo, hi, step: int, seed: int, stream=None):
                               n, int(step), int(seed), ctypes.c_void_p(d_out.data_ptr()),
                               ctypes.c_void_p(d_xi.data_ptr()), _stream_ptr(stream)))
     return d_out.cpu().numpy().view(np.uint32), d_xi.cpu().numpy()
+
+
+NOALLOC_MAX_PARTICLES = 32768
+NOALLOC_MAX_CELLS = 32767
+
+
+def forces_noalloc(pos, vel, L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, step=0,
+                   out=None, stream=None):
+    """Pair forces from a caller-held CUDA state through dpd_forces_noalloc,
+    which allocates no device memory (its scratch is a static device array).
+
+    pos, vel: n x 3 float32 CUDA tensors; returns (or fills ``out``) an n x 3
+    CUDA tensor.  The work is enqueued on ``stream`` without synchronising."""
+    import torch
+    if not (_is_cuda_tensor(pos) and _is_cuda_tensor(vel)):
+        raise ValueError("pos and vel must be CUDA tensors")
+    n = int(pos.shape[0])
+    pp, _, kp = _vec3_arg(pos, n)
+    vv, _, kv = _vec3_arg(vel, n)
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+    L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+    box = (ctypes.c_double * 3)(*L3)
+    check(lib().dpd_forces_noalloc(n, pp, vv, box, a, gamma, kT, rc, dt, int(seed), int(step),
+                                   ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
