@@ -186,6 +186,63 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, stream, world, rank):
+    """512-box mix: one packed batch vs the same boxes one at a time with
+    their own single-box contexts (same stream), both with states resident."""
+    import torch
+
+    import paper_1911_04712_gb300.batch as B
+    import paper_1911_04712_gb300.dpd as dpd
+    from paper_1911_04712_gb300.workloads import box_mix, uniform_box_state
+
+    specs = box_mix(args.nbox, master_seed=args.seed)
+    if world > 1:                       # shard boxes over ranks, no collective
+        specs = specs[rank::world]
+    states = [uniform_box_state(s.L, rho=s.rho, kT=s.kT, seed=s.seed) for s in specs]
+    n_tot = sum(len(x) for x, _ in states)
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
+             for s, st in zip(specs, states)]
+    bt = B.Batch(descs, stream=stream)
+    for k, (x, v) in enumerate(states):
+        bt.set_state(k, x, v)
+    bt.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bt.step(args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    stage_ms = bt.profile(10)
+    bt.close()
+
+    boxes = []
+    for s, (x, v) in zip(specs, states):
+        b = dpd.Box(s.L, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed, stream=stream)
+        b.set_state(x, v)
+        b.step(args.warmup)
+        boxes.append(b)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for b in boxes:                      # one box at a time, each to completion
+        b.step(args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    for b in boxes:
+        b.close()
+    rate_b = n_tot * args.batch_steps / (ms_b / 1000.0)
+    rate_s = n_tot * args.batch_steps / (ms_s / 1000.0)
+    return {"workload": f"box mix: {len(specs)} boxes, L~U{{6..24}}, rho in {{3,4,5}}, "
+                        f"a~U[10,80], gamma~U[2,8], kT~U[0.5,2], dt=0.005",
+            "boxes": len(specs), "particles": n_tot, "steps": args.batch_steps,
+            "value": rate_b, "unit": UNIT, "ms_per_step": ms_b / args.batch_steps,
+            "one_box_at_a_time": {"value": rate_s, "ms_per_step": ms_s / args.batch_steps},
+            "speedup_vs_one_at_a_time": rate_b / rate_s,
+            "stages_ms": {k: round(t, 5) for k, t in zip(dpd.STAGE_NAMES, stage_ms)},
+            "gpu_launches_per_step": dpd.KERNELS_PER_STEP}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -294,6 +351,15 @@ def run_native(args):
                        "get_state to pinned host"}
         ebox.close()
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, stream, world, rank)
+        if dist:
+            t = torch.tensor([batched["value"], batched["one_box_at_a_time"]["value"]],
+                             device="cuda", dtype=torch.float64)
+            dist.all_reduce(t)                 # boxes are sharded: aggregate rates add
+            batched["value"], batched["one_box_at_a_time"]["value"] = float(t[0]), float(t[1])
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.cpu_L, rho, args.cpu_steps)
@@ -319,6 +385,7 @@ def run_native(args):
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": base,
+            "batched": batched,
         }
         print(json.dumps(out), flush=True)
     box.close()
@@ -345,6 +412,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-L", type=float, default=32.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--nbox", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     args = ap.parse_args()

@@ -92,6 +92,9 @@ typedef struct dpd_ctx dpd_ctx;
 #define DPD_PARAM_STAGE_CAP 10    /* staged particles per block, 64..4096; 0 (default) = by density;
                                      blocks whose neighbourhood exceeds it read global memory */
 
+#define DPD_PARAM_FORCE_VARIANT 11 /* direct force-kernel variant 0..DPD_NUM_FORCE_VARIANTS-1, or -1
+                                      (default) to pick per density band from the tuning table */
+
 #define DPD_STENCIL_FULL 0  /* 27 cells, each thread sums its own pairs: no atomics,
                                bitwise reproducible */
 #define DPD_STENCIL_HALF 1  /* 13 cells + own cell, Newton's third law with atomics
@@ -175,6 +178,74 @@ DPD_API int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms);
  * values.  Runs on the given stream (NULL = default) and synchronises it. */
 DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uint64_t step, uint64_t seed,
                   uint32_t *out, float *xi, void *stream);
+
+/* --------------------------------------------------------- kernel tuning */
+/* The direct force kernel comes in variants that differ in threads per
+ * block and pair-list entries per thread.  A process-wide table, one per
+ * stencil, maps density bands (upper bounds of rho = N/V, increasing; the
+ * last band also takes every higher density) to a variant.  Contexts and
+ * batches pick their variants from it when their state is laid out, or
+ * after dpd_tuning_apply.  The package's autotuner measures the variants
+ * per band on the GPU and sets the table. */
+#define DPD_NUM_FORCE_VARIANTS 7
+#define DPD_MAX_DENSITY_BANDS 8
+/* threads per block and list capacity of variant v; DPD_ERR_ARG if out of range */
+DPD_API int dpd_force_variant_info(int v, int *threads, int *list_capacity);
+/* set the table of `stencil` (DPD_STENCIL_FULL/HALF): nbands in 1..DPD_MAX_DENSITY_BANDS */
+DPD_API int dpd_tuning_set(int stencil, int nbands, const double *rho_upper, const int *variant);
+/* copy at most `max` bands of the table; *nbands receives the table's length */
+DPD_API int dpd_tuning_get(int stencil, int max, double *rho_upper, int *variant, int *nbands);
+
+/* ============================================================ many boxes */
+/* A batch steps many independent periodic boxes together: their particles
+ * and cells are packed into one set of arrays (per-box slot and cell
+ * offsets, boxes ordered by density band), every stage of a step is one
+ * launch over all boxes, and steps are replayed from CUDA graphs.  Each box
+ * gives exactly the trajectory it would give alone in a dpd_ctx with the
+ * same parameters and the same stencil/variant (bitwise for the full
+ * stencil). */
+typedef struct dpd_batch dpd_batch;
+
+typedef struct {
+    double box[3];       /* edges, each >= 3 rc */
+    double a, gamma, kT, rc, dt;
+    uint64_t seed;
+    int64_t n;           /* particles in this box */
+    int64_t steps;       /* steps this box takes in total; <= 0: no limit */
+    double kexp;         /* weight exponent; 0 means 1 */
+    double mass;         /* particle mass; 0 means 1 */
+    double body_force;   /* body-force magnitude (0: none) */
+    int body_mode;       /* 0 none, 1 constant, 2 periodic Poiseuille (Sec. 4.2) */
+    int flow_axis;       /* axis of the body force */
+    int grad_axis;       /* axis on which the Poiseuille force switches sign */
+    int pad_;
+} dpd_box_desc;
+
+/* Create a batch of nbox boxes and allocate its device memory.
+ * Errors: DPD_ERR_ARG (a descriptor is invalid; the message names the box),
+ * DPD_ERR_NOMEM, DPD_ERR_CUDA. */
+DPD_API int dpd_batch_create(dpd_batch **out, int nbox, const dpd_box_desc *descs);
+DPD_API int dpd_batch_destroy(dpd_batch *b);
+DPD_API int dpd_batch_set_stream(dpd_batch *b, void *stream);
+/* DPD_PARAM_STENCIL, DPD_PARAM_FORCE_TILES, DPD_PARAM_TILE_CELLS,
+ * DPD_PARAM_STAGE_CAP, DPD_PARAM_FORCE_VARIANT, or DPD_BATCH_GRAPH_CHUNK
+ * (steps per captured graph, >= 1) */
+#define DPD_BATCH_GRAPH_CHUNK 100
+DPD_API int dpd_batch_set_option(dpd_batch *b, int key, double value);
+/* Load box `box` (n of its descriptor x 3 FP32, host or device); ids 0..n-1
+ * within the box; the box's step counter restarts at 0.  The cell lists and
+ * forces of loaded boxes are built at the next step or read. */
+DPD_API int dpd_batch_set_state(dpd_batch *b, int box, const float *pos, const float *vel,
+                                int where);
+/* Advance every box by nsteps (a box with a step limit stops at it).
+ * Errors: DPD_ERR_STATE while some box has not been loaded. */
+DPD_API int dpd_batch_step(dpd_batch *b, int64_t nsteps);
+DPD_API int dpd_batch_get_state(dpd_batch *b, int box, float *pos, float *vel, int where);
+DPD_API int dpd_batch_get_forces(dpd_batch *b, int box, float *force, int where);
+/* Statistics of every box (out has nbox entries, in the order of the descriptors). */
+DPD_API int dpd_batch_get_stats(dpd_batch *b, dpd_stats *out);
+DPD_API int dpd_batch_profile_steps(dpd_batch *b, int64_t nsteps, double *stage_ms);
+DPD_API int dpd_batch_num_boxes(const dpd_batch *b);
 
 /* ------------------------------------------------- forces without allocation */
 /* The paper has no counterpart to this call; it exists for callers that

@@ -110,6 +110,11 @@ int dpd_set_param(dpd_ctx *ctx, int key, double value) {
       ctx->stage_cap = cap;
       return DPD_OK;
     }
+    case DPD_PARAM_FORCE_VARIANT:
+      if (!(value >= -1.0 && value < DPD_NUM_FORCE_VARIANTS) || value != std::floor(value))
+        return dpd::set_error(DPD_ERR_ARG, "force variant must be -1..%d",
+                              DPD_NUM_FORCE_VARIANTS - 1);
+      return ctx->eng.set_variant((int)value);
     default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
   }
   if (rc) return rc;
@@ -137,6 +142,9 @@ int dpd_get_param(const dpd_ctx *ctx, int key, double *value) {
     case DPD_PARAM_FORCE_TILES: *value = cfg.tiles ? 1.0 : 0.0; break;
     case DPD_PARAM_TILE_CELLS: *value = ctx->loaded ? cfg.grid.tc : ctx->tile_cells; break;
     case DPD_PARAM_STAGE_CAP: *value = ctx->loaded ? cfg.grid.stage_cap : ctx->stage_cap; break;
+    case DPD_PARAM_FORCE_VARIANT:
+      *value = (ctx->loaded && cfg.nbands > 0) ? cfg.band[0].variant : ctx->eng.variant_override();
+      break;
     default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
   }
   return DPD_OK;

@@ -139,7 +139,48 @@ int Engine::set_stencil(int stencil) {
   if (stencil != cfg_.stencil) {
     cfg_.stencil = stencil;
     drop_graph();
+    if (!boxes_.empty()) return build_bands();
   }
+  return DPD_OK;
+}
+
+int Engine::set_variant(int variant) {
+  if (variant < -1 || variant >= kNumForceVariants)
+    return set_error(DPD_ERR_ARG, "force variant must be -1..%d", kNumForceVariants - 1);
+  variant_override_ = variant;
+  drop_graph();
+  return boxes_.empty() ? DPD_OK : build_bands();
+}
+
+int Engine::refresh_bands() {
+  drop_graph();
+  return boxes_.empty() ? DPD_OK : build_bands();
+}
+
+// Group consecutive boxes that use the same direct-kernel variant into
+// bands (contiguous slot ranges), one force launch each.
+int Engine::build_bands() {
+  const int nb = nbox();
+  std::vector<ForceBand> runs;
+  for (int b = 0; b < nb; ++b) {
+    const BoxDev &B = boxes_[b];
+    const double rho = (double)B.np / ((double)B.L[0] * B.L[1] * B.L[2]);
+    const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(cfg_.stencil, rho);
+    if (!runs.empty() && runs.back().variant == v)
+      runs.back().slot1 = pbase_[b + 1];
+    else
+      runs.push_back(ForceBand{pbase_[b], pbase_[b + 1], v});
+  }
+  if ((int)runs.size() > kMaxBands) {
+    // too fragmented (boxes not ordered by band): one launch with the
+    // variant that covers the most particles
+    std::vector<long long> cover(kNumForceVariants, 0);
+    for (const auto &r : runs) cover[r.variant] += r.slot1 - r.slot0;
+    const int best = (int)(std::max_element(cover.begin(), cover.end()) - cover.begin());
+    runs.assign(1, ForceBand{0, ntot_, best});
+  }
+  cfg_.nbands = (int)runs.size();
+  for (int k = 0; k < cfg_.nbands; ++k) cfg_.band[k] = runs[k];
   return DPD_OK;
 }
 
@@ -344,7 +385,9 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
                                cudaMemcpyHostToDevice, stream_));
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.pbase, pbase_.data(), pbase_.size() * sizeof(int),
                                cudaMemcpyHostToDevice, stream_));
-  return build_tiles();
+  int rc2 = build_tiles();
+  if (rc2) return rc2;
+  return build_bands();
 }
 
 int Engine::update_params(const std::vector<BoxParams> &params) {

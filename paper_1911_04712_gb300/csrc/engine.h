@@ -69,6 +69,12 @@ class Engine {
   // neighbours from global memory; tc / stage_cap > 0 override the choice by
   // density (cells per tile, staged particles per block).
   int set_tiling(int use_tiles, int tc, int stage_cap);
+  // Direct force-kernel variant: -1 (default) picks per box from the tuning
+  // table by density; 0..kNumForceVariants-1 forces one for every box.
+  int set_variant(int variant);
+  int variant_override() const { return variant_override_; }
+  // Re-derive the per-band variants (after the tuning table changed).
+  int refresh_bands();
   const StepConfig &step_config() const { return cfg_; }
 
   // Lay out boxes: particle counts per box decide the slot ranges.  Allocates
@@ -126,6 +132,8 @@ class Engine {
   int4 *d_tiles_ = nullptr;
   size_t cap_tiles_ = 0;
   int build_tiles();
+  int build_bands();
+  int variant_override_ = -1;
   std::vector<BoxParams> params_;
   std::vector<BoxDev> boxes_;
   std::vector<int> pbase_;

@@ -1,0 +1,661 @@
+// Force kernels of the DPD step: pair forces (Sec. 2.1, Eqs. 2-5) over the
+// cell list (Sec. 3.2), in variants that differ in block size and pair-list
+// capacity (chosen per density band from a tuning table), plus the optional
+// shared-memory staged tiles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "dpd_device.cuh"
+#include "kernels.h"
+
+namespace dpd {
+
+constexpr int kTileListCap = 24;
+
+static inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ force
+// Pair lists: each thread appends the neighbours found inside rc to its own
+// column of a shared-memory list (entry k of thread t at lst[k * NT + t], NT threads),
+// then drains the list computing the pair forces.  An entry is 4 bytes: the
+// neighbour slot j (26 bits) and the periodic-image code of the pair:
+//   bit 26/28/30  the neighbour image is r_j - L on x/y/z (j near the top face)
+//   bit 27/29/31  i is taken at r_i - L on x/y/z (i near the top face)
+// Both subtractions are exact in FP32 (the shifted coordinate lies in
+// [2L/3, L)), so no rounding error of size ulp(L) enters r_ij.
+constexpr uint32_t kSlotMask = (1u << 26) - 1u;
+constexpr uint32_t kCodeJX = 1u << 26, kCodeIX = 1u << 27, kCodeJY = 1u << 28,
+                   kCodeIY = 1u << 29, kCodeJZ = 1u << 30, kCodeIZ = 1u << 31;
+
+// Candidate pass over slots [j0, j1): appends every j with 0 < r_ij^2 < rc^2.
+// The append is branch-free (the slot is written every iteration and kept only
+// on a hit), so the lanes of a warp stay converged.  Returns the slot at which
+// the list became full, or -1 when the range was scanned completely.
+template <bool JSHIFT, int NT, int CAP>
+__device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0, int j1,
+                                          float ax, float ay, float az, float jsx, float jsy,
+                                          float jsz, float rc2, uint32_t code,
+                                          uint32_t *__restrict__ lst, int &cnt) {
+  for (int j = j0; j < j1; ++j) {
+    const float4 pj = __ldg(pos + j);
+    float dx, dy, dz;
+    if constexpr (JSHIFT) {
+      dx = ax - (pj.x - jsx);
+      dy = ay - (pj.y - jsy);
+      dz = az - (pj.z - jsz);
+    } else {
+      dx = ax - pj.x;
+      dy = ay - pj.y;
+      dz = az - pj.z;
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool hit = (r2 < rc2) & (r2 > 0.0f);
+    lst[cnt * NT] = (uint32_t)j | code;
+    cnt += hit ? 1 : 0;
+    if (cnt == CAP) return j;
+  }
+  return -1;
+}
+
+// Force on one target particle in slot p from the 27-cell (full) or 13-cell
+// + own-cell (half) neighbourhood, reading neighbours from global memory.
+// Every lane of the warp must call this (dead lanes with alive = false) since
+// list drains are decided warp-wide.
+template <bool HALF, int NT, int CAP>
+__device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,
+                                             int p, bool alive, uint32_t *__restrict__ lst) {
+  constexpr int FLUSH = CAP / 2;  // a warp drains its lists after a row once any lane exceeds this
+  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+  if (alive) {
+    pi = P.pos[p];
+    vi = P.vel[p];
+  }
+  int cx, cy, cz;
+  unpack_cell(__float_as_int(vi.w), cx, cy, cz);
+  const uint32_t idi = __float_as_uint(pi.w);
+  const uint32_t slo = (uint32_t)S.step, shi = (uint32_t)(S.step >> 32);
+  const float Lx = B.L[0], Ly = B.L[1], Lz = B.L[2];
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+
+  float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
+  int cnt = 0;
+
+  auto drain = [&]() {
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t e = lst[k * NT];
+      const int j = (int)(e & kSlotMask);
+      const float4 pj = __ldg(P.pos + j);
+      const float4 vj = __ldg(P.vel + j);
+      float dx, dy, dz;
+      if (e & ~kSlotMask) {  // pair across a box face (rare)
+        dx = ((e & kCodeIX) ? pi.x - Lx : pi.x) - ((e & kCodeJX) ? pj.x - Lx : pj.x);
+        dy = ((e & kCodeIY) ? pi.y - Ly : pi.y) - ((e & kCodeJY) ? pj.y - Ly : pj.y);
+        dz = ((e & kCodeIZ) ? pi.z - Lz : pi.z) - ((e & kCodeJZ) ? pj.z - Lz : pj.z);
+      } else {
+        dx = pi.x - pj.x;
+        dy = pi.y - pj.y;
+        dz = pi.z - pj.z;
+      }
+      const uint32_t idj = __float_as_uint(pj.w);
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv;
+      const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
+      const float wR = (B.kexp == 1.0f) ? w : powf(w, B.kexp);
+      const float ev = fmaf(dx, vi.x - vj.x, fmaf(dy, vi.y - vj.y, dz * (vi.z - vj.z))) * rinv;
+      const uint32_t u = pair_word(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
+      const float fc = B.a * w;
+      const float s = fmaf(B.sig * wR, noise_int(u), fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
+      const float gx = s * dx, gy = s * dy, gz = s * dz;
+      fx += gx;
+      fy += gy;
+      fz += gz;
+      const float vterm = fc * r;
+      vir += vterm;
+      if constexpr (HALF) {
+        atomicAdd(P.frc + j, make_float4(-gx, -gy, -gz, vterm));
+      }
+    }
+    cnt = 0;
+  };
+
+  // One contiguous slot range with a fixed image code; drains when the list fills.
+  auto range = [&](int j0, int j1, float ax, float ay, float az, float jsx, float jsy, float jsz,
+                   uint32_t code) {
+    while (j0 < j1) {
+      const int stop = (code & (kCodeJX | kCodeJY | kCodeJZ))
+                           ? scan_range<true, NT, CAP>(P.pos, j0, j1, ax, ay, az, jsx, jsy, jsz,
+                                                       B.rc2, code, lst, cnt)
+                           : scan_range<false, NT, CAP>(P.pos, j0, j1, ax, ay, az, 0.f, 0.f, 0.f,
+                                                        B.rc2, code, lst, cnt);
+      if (stop < 0) break;
+      drain();
+      j0 = stop + 1;
+    }
+  };
+
+  // Cells cx-1..cx+1 (or cx..cx+1 from `xlo`) of one row; one range unless
+  // the row crosses an x face.
+  auto row = [&](int rowbase, float ay, float az, float jsy, float jsz, uint32_t code) {
+    if (cx >= 1 && cx <= nx - 2) {
+      range(__ldg(P.start + rowbase + cx - 1), __ldg(P.start + rowbase + cx + 2), pi.x, ay, az,
+            0.f, jsy, jsz, code);
+    } else {
+      for (int dxc = -1; dxc <= 1; ++dxc) {
+        int x = cx + dxc;
+        float ax = pi.x, jsx = 0.f;
+        uint32_t c = code;
+        if (x < 0) {
+          x += nx;
+          jsx = Lx;
+          c |= kCodeJX;
+        } else if (x >= nx) {
+          x -= nx;
+          ax = pi.x - Lx;
+          c |= kCodeIX;
+        }
+        range(__ldg(P.start + rowbase + x), __ldg(P.start + rowbase + x + 1), ax, ay, az, jsx,
+              jsy, jsz, c);
+      }
+    }
+  };
+
+  auto rowfor = [&](int dy, int dz) {
+    int z = cz + dz, y = cy + dy;
+    float az = pi.z, jsz = 0.f, ay = pi.y, jsy = 0.f;
+    uint32_t code = 0;
+    if (z < 0) {
+      z += nz;
+      jsz = Lz;
+      code |= kCodeJZ;
+    } else if (z >= nz) {
+      z -= nz;
+      az = pi.z - Lz;
+      code |= kCodeIZ;
+    }
+    if (y < 0) {
+      y += ny;
+      jsy = Ly;
+      code |= kCodeJY;
+    } else if (y >= ny) {
+      y -= ny;
+      ay = pi.y - Ly;
+      code |= kCodeIY;
+    }
+    if (alive) row(B.cellBase + (z * ny + y) * nx, ay, az, jsy, jsz, code);
+    if (__any_sync(0xffffffffu, cnt > FLUSH)) drain();
+  };
+
+  if constexpr (!HALF) {
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy) rowfor(dy, dz);
+  } else {
+    // Half stencil: own cell (slots after p) and cell cx+1 of the own row, the
+    // row dy=+1 of the own plane, and the three rows of the plane dz=+1.
+    if (alive) {
+      const int rowbase = B.cellBase + (cz * ny + cy) * nx;
+      if (cx + 1 <= nx - 1) {
+        range(p + 1, __ldg(P.start + rowbase + cx + 2), pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, 0u);
+      } else {
+        range(p + 1, __ldg(P.start + rowbase + cx + 1), pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, 0u);
+        range(__ldg(P.start + rowbase), __ldg(P.start + rowbase + 1), pi.x - Lx, pi.y, pi.z, 0.f,
+              0.f, 0.f, kCodeIX);
+      }
+    }
+    if (__any_sync(0xffffffffu, cnt > FLUSH)) drain();
+    rowfor(1, 0);
+    rowfor(-1, 1);
+    rowfor(0, 1);
+    rowfor(1, 1);
+  }
+  drain();
+
+  if (!alive) return;
+  if (B.fb_mode != 0) {  // body force (Sec. 4.2 periodic Poiseuille, or constant)
+    float add = B.fb;
+    if (B.fb_mode == 2) {
+      const float xg = (B.fb_grad == 0) ? pi.x : (B.fb_grad == 1) ? pi.y : pi.z;
+      add = (xg <= B.fb_half) ? -B.fb : B.fb;
+    }
+    if (B.fb_flow == 0)
+      fx += add;
+    else if (B.fb_flow == 1)
+      fy += add;
+    else
+      fz += add;
+  }
+  if constexpr (HALF) {
+    atomicAdd(P.frc + p, make_float4(fx, fy, fz, vir));
+  } else {
+    P.frc[p] = make_float4(fx, fy, fz, vir);
+  }
+}
+
+// One thread per target slot in [slot0, slot1).
+template <bool SINGLE, bool HALF, int NT, int CAP>
+__global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
+  __shared__ uint32_t smem_list[CAP * NT];
+  const int p = slot0 + blockIdx.x * NT + threadIdx.x;
+  bool alive = p < slot1;
+  const int b = (!SINGLE && alive) ? find_box(P.pbase, P.nbox, p) : 0;
+  const BoxDev B = box_of<SINGLE>(P, b);
+  const BoxState S = P.st[b];
+  alive = alive && S.adv;
+  force_direct<HALF, NT, CAP>(P, B, S, p, alive, smem_list + threadIdx.x);
+}
+
+// ------------------------------------------------------- staged force tiles
+// A thread block owns a run of `nc` consecutive cells (cx0 .. cx0+nc-1) of
+// one x-row of one box.  It copies the 9 neighbouring row segments -- cells
+// cx0-1 .. cx0+nc of rows (cy+dy, cz+dz) -- into shared memory, positions
+// and velocities, then every thread takes a target particle of its own row
+// and scans its 27 cells from shared memory.
+//
+// Periodic images: a neighbour image r_j - L (j in the top cells, row or
+// cell wrapped below) is stored pre-shifted, which is exact in FP32 because
+// that coordinate lies in [2L/3, L).  An image r_j + L is never formed:
+// the target uses r_i - L instead (exact for the same reason): per row for
+// y and z, per thread for the wrapped cell 0 at the x end of the row.
+struct TileRow {
+  int rb;                  // packed index of the row's first cell
+  int gBeg, lenBeg;        // wrapped cell nx-1 (x image - L), only when cx0 == 0
+  int gMain, lenMain;      // cells max(cx0-1,0) .. min(cx0+nc, nx-1)
+  int gEnd, lenEnd;        // wrapped cell 0, only when cx0 + nc == nx
+  int off;                 // first shared-memory slot of the row
+  float jsy, jsz;          // pre-shift of stored y / z (0 or L)
+  uint32_t ish;            // i-shift code bits for y / z (kCodeIY / kCodeIZ)
+  int pad;
+};
+
+// Scan staged candidates [j0, j1) against one target; entries are the staged
+// index (16 bits) plus i-shift code bits.  Returns the index at which the
+// list filled, or -1.
+__device__ __forceinline__ int scan_staged(const float4 *__restrict__ sPos, int j0, int j1,
+                                           float ax, float ay, float az, float rc2, uint32_t code,
+                                           uint32_t *__restrict__ lst, int stride, int &cnt,
+                                           int cap) {
+  for (int j = j0; j < j1; ++j) {
+    const float4 pj = sPos[j];
+    const float dx = ax - pj.x, dy = ay - pj.y, dz = az - pj.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool hit = (r2 < rc2) & (r2 > 0.0f);
+    lst[cnt * stride] = (uint32_t)j | code;
+    cnt += hit ? 1 : 0;
+    if (cnt == cap) return j;
+  }
+  return -1;
+}
+
+template <bool SINGLE>
+__global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid G) {
+  extern __shared__ float4 tile_smem[];
+  __shared__ TileRow rows[9];
+  __shared__ int sB[9][kTileMaxCells + 3];
+  __shared__ int sTotal;
+
+  const int tid = threadIdx.x;
+  int b, cy, cz, cx0, nc;
+  BoxDev B;
+  if constexpr (SINGLE) {
+    B = P.single;
+    b = 0;
+    const int t = blockIdx.x;
+    const int rowi = t / G.tpr;
+    cx0 = (t - rowi * G.tpr) * G.tc;
+    nc = min(G.tc, B.n[0] - cx0);
+    cy = rowi % B.n[1];
+    cz = rowi / B.n[1];
+  } else {
+    const int4 d = G.list[blockIdx.x];
+    b = d.x;
+    cy = d.y;
+    cz = d.z;
+    cx0 = d.w & 0xFFFF;
+    nc = d.w >> 16;
+    B = P.boxes[b];
+  }
+  const BoxState S = P.st[b];
+  if (!S.adv) return;  // uniform over the block
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const float Lx = B.L[0], Ly = B.L[1], Lz = B.L[2];
+  const int m0 = max(cx0 - 1, 0), m1 = min(cx0 + nc, nx - 1);
+
+  if (tid < 9) {
+    const int dz = tid / 3 - 1, dy = tid % 3 - 1;
+    int zz = cz + dz, yy = cy + dy;
+    TileRow R;
+    R.jsy = 0.f;
+    R.jsz = 0.f;
+    R.ish = 0u;
+    if (zz < 0) {
+      zz += nz;
+      R.jsz = Lz;
+    } else if (zz >= nz) {
+      zz -= nz;
+      R.ish |= kCodeIZ;
+    }
+    if (yy < 0) {
+      yy += ny;
+      R.jsy = Ly;
+    } else if (yy >= ny) {
+      yy -= ny;
+      R.ish |= kCodeIY;
+    }
+    R.rb = B.cellBase + (zz * ny + yy) * nx;
+    R.gMain = __ldg(P.start + R.rb + m0);
+    R.lenMain = __ldg(P.start + R.rb + m1 + 1) - R.gMain;
+    R.gBeg = 0;
+    R.lenBeg = 0;
+    if (cx0 == 0) {
+      R.gBeg = __ldg(P.start + R.rb + nx - 1);
+      R.lenBeg = __ldg(P.start + R.rb + nx) - R.gBeg;
+    }
+    R.gEnd = 0;
+    R.lenEnd = 0;
+    if (cx0 + nc == nx) {
+      R.gEnd = __ldg(P.start + R.rb);
+      R.lenEnd = __ldg(P.start + R.rb + 1) - R.gEnd;
+    }
+    R.off = 0;
+    R.pad = 0;
+    rows[tid] = R;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int off = 0;
+    for (int r = 0; r < 9; ++r) {
+      rows[r].off = off;
+      off += rows[r].lenBeg + rows[r].lenMain + rows[r].lenEnd;
+    }
+    sTotal = off;
+  }
+  __syncthreads();
+  const int total = sTotal;
+  const bool staged = total <= G.stage_cap;
+  float4 *sPos = tile_smem;
+  float4 *sVel = tile_smem + G.stage_cap;
+  uint32_t *lst = reinterpret_cast<uint32_t *>(tile_smem + 2 * G.stage_cap);
+
+  // targets: the tile's own cells in the centre row (rows[4] is dy = dz = 0)
+  const int t0 = __ldg(P.start + rows[4].rb + cx0);
+  const int t1 = __ldg(P.start + rows[4].rb + cx0 + nc);
+
+  if (!staged) {
+    // too many particles to stage: read neighbours from global memory
+    for (int base = t0; base < t1; base += kTileThreads) {
+      const int p = base + tid;
+      force_direct<false, kTileThreads, kTileListCap>(P, B, S, p, p < t1, lst + tid);
+    }
+    return;
+  }
+
+  // cell boundaries inside the staged rows: sB[r][k] = first staged slot of
+  // virtual cell cx0 - 1 + k, k = 0 .. nc + 2
+  for (int idx = tid; idx < 9 * (nc + 3); idx += kTileThreads) {
+    const int r = idx / (nc + 3), k = idx - r * (nc + 3);
+    const TileRow &R = rows[r];
+    const int x = cx0 - 1 + k;
+    int v;
+    if (x < m0)
+      v = R.off;
+    else if (x <= m1 + 1)
+      v = R.off + R.lenBeg + (__ldg(P.start + R.rb + x) - R.gMain);
+    else
+      v = R.off + R.lenBeg + R.lenMain + R.lenEnd;
+    sB[r][k] = v;
+  }
+  // copy the neighbourhood (coalesced float4 loads)
+  for (int r = 0; r < 9; ++r) {
+    const TileRow &R = rows[r];
+    const int len = R.lenBeg + R.lenMain + R.lenEnd;
+    for (int i = tid; i < len; i += kTileThreads) {
+      int g;
+      float xs = 0.f;
+      if (i < R.lenBeg) {
+        g = R.gBeg + i;
+        xs = Lx;
+      } else if (i < R.lenBeg + R.lenMain) {
+        g = R.gMain + (i - R.lenBeg);
+      } else {
+        g = R.gEnd + (i - R.lenBeg - R.lenMain);
+      }
+      float4 q = __ldg(P.pos + g);
+      q.x -= xs;
+      q.y -= R.jsy;
+      q.z -= R.jsz;
+      sPos[R.off + i] = q;
+      sVel[R.off + i] = __ldg(P.vel + g);
+    }
+  }
+  __syncthreads();
+
+  const float rc2 = B.rc2;
+  const uint32_t slo = (uint32_t)S.step, shi = (uint32_t)(S.step >> 32);
+  const bool xend = (cx0 + nc == nx);
+  for (int base = t0; base < t1; base += kTileThreads) {
+    const int p = base + tid;
+    const bool alive = p < t1;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+    if (alive) {
+      pi = __ldg(P.pos + p);
+      vi = __ldg(P.vel + p);
+    }
+    int cx, cyy, czz;
+    unpack_cell(__float_as_int(vi.w), cx, cyy, czz);
+    const int kt = cx - cx0 + 1;  // virtual cell of the target, 1..nc
+    const uint32_t idi = __float_as_uint(pi.w);
+    float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
+    int cnt = 0;
+    uint32_t *my = lst + tid;
+
+    auto drain = [&]() {
+      for (int k = 0; k < cnt; ++k) {
+        const uint32_t e = my[k * kTileThreads];
+        const int j = (int)(e & 0xFFFFu);
+        const float4 pj = sPos[j];
+        const float4 vj = sVel[j];
+        const float ax = (e & kCodeIX) ? pi.x - Lx : pi.x;
+        const float ay = (e & kCodeIY) ? pi.y - Ly : pi.y;
+        const float az = (e & kCodeIZ) ? pi.z - Lz : pi.z;
+        const float dx = ax - pj.x, dy = ay - pj.y, dz = az - pj.z;
+        const uint32_t idj = __float_as_uint(pj.w);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
+        const float wR = (B.kexp == 1.0f) ? w : powf(w, B.kexp);
+        const float ev =
+            fmaf(dx, vi.x - vj.x, fmaf(dy, vi.y - vj.y, dz * (vi.z - vj.z))) * rinv;
+        const uint32_t u = pair_word(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
+        const float fc = B.a * w;
+        const float sc = fmaf(B.sig * wR, noise_int(u), fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
+        fx = fmaf(sc, dx, fx);
+        fy = fmaf(sc, dy, fy);
+        fz = fmaf(sc, dz, fz);
+        vir = fmaf(fc, r, vir);
+      }
+      cnt = 0;
+    };
+
+    for (int r = 0; r < 9; ++r) {
+      if (alive) {
+        const TileRow &R = rows[r];
+        const float ay = (R.ish & kCodeIY) ? pi.y - Ly : pi.y;
+        const float az = (R.ish & kCodeIZ) ? pi.z - Lz : pi.z;
+        int j0 = sB[r][kt - 1];
+        const int j1 = sB[r][kt + 2];
+        // the wrapped cell 0 past the x end is seen from r_i - L
+        const int jx = (xend && kt == nc) ? sB[r][nc + 1] : j1;
+        while (j0 < jx) {
+          const int stop = scan_staged(sPos, j0, jx, pi.x, ay, az, rc2, R.ish, my, kTileThreads,
+                                       cnt, kTileListCap);
+          if (stop < 0) break;
+          drain();
+          j0 = stop + 1;
+        }
+        j0 = max(j0, jx);
+        while (j0 < j1) {
+          const int stop = scan_staged(sPos, j0, j1, pi.x - Lx, ay, az, rc2, R.ish | kCodeIX, my,
+                                       kTileThreads, cnt, kTileListCap);
+          if (stop < 0) break;
+          drain();
+          j0 = stop + 1;
+        }
+      }
+      if (__any_sync(0xffffffffu, cnt > kTileListCap / 2)) drain();
+    }
+    drain();
+    if (alive) {
+      if (B.fb_mode != 0) {
+        float add = B.fb;
+        if (B.fb_mode == 2) {
+          const float xg = (B.fb_grad == 0) ? pi.x : (B.fb_grad == 1) ? pi.y : pi.z;
+          add = (xg <= B.fb_half) ? -B.fb : B.fb;
+        }
+        if (B.fb_flow == 0)
+          fx += add;
+        else if (B.fb_flow == 1)
+          fy += add;
+        else
+          fz += add;
+      }
+      P.frc[p] = make_float4(fx, fy, fz, vir);
+    }
+  }
+}
+
+// ================================================================ variants
+// Direct-kernel variants: (threads per block, pair-list entries per thread).
+struct VariantInfo {
+  int threads, cap;
+};
+static const VariantInfo kVariants[kNumForceVariants] = {
+    {128, 24}, {128, 16}, {128, 32}, {256, 24}, {64, 24}, {64, 32}, {256, 32}};
+
+int force_variant_info(int v, int *threads, int *cap) {
+  if (v < 0 || v >= kNumForceVariants) return -1;
+  *threads = kVariants[v].threads;
+  *cap = kVariants[v].cap;
+  return 0;
+}
+
+template <bool SINGLE, bool HALF, int NT, int CAP>
+static void launch_k(const Packed &P, int s0, int s1, cudaStream_t s) {
+  if (s1 > s0) k_force<SINGLE, HALF, NT, CAP><<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
+}
+
+template <bool SINGLE, bool HALF>
+static void launch_variant(int v, const Packed &P, int s0, int s1, cudaStream_t s) {
+  switch (v) {
+    case 1: launch_k<SINGLE, HALF, 128, 16>(P, s0, s1, s); break;
+    case 2: launch_k<SINGLE, HALF, 128, 32>(P, s0, s1, s); break;
+    case 3: launch_k<SINGLE, HALF, 256, 24>(P, s0, s1, s); break;
+    case 4: launch_k<SINGLE, HALF, 64, 24>(P, s0, s1, s); break;
+    case 5: launch_k<SINGLE, HALF, 64, 32>(P, s0, s1, s); break;
+    case 6: launch_k<SINGLE, HALF, 256, 32>(P, s0, s1, s); break;
+    default: launch_k<SINGLE, HALF, 128, 24>(P, s0, s1, s); break;
+  }
+}
+
+size_t tile_smem_bytes(int stage_cap) {
+  return (size_t)stage_cap * 2 * sizeof(float4) +
+         (size_t)kTileListCap * kTileThreads * sizeof(uint32_t);
+}
+
+cudaError_t prepare_device() {
+  // staged tiles may use more than the default 48 KB of dynamic shared memory
+  const int maxb = 200 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_force_tiles<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_force_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              maxb);
+}
+
+cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s) {
+  const bool single = (P.nbox == 1);
+  const bool half = (cfg.stencil == 1);
+  if (!half && cfg.tiles && cfg.grid.ntiles > 0) {
+    const size_t smem = tile_smem_bytes(cfg.grid.stage_cap);
+    if (single)
+      k_force_tiles<true><<<cfg.grid.ntiles, kTileThreads, smem, s>>>(P, cfg.grid);
+    else
+      k_force_tiles<false><<<cfg.grid.ntiles, kTileThreads, smem, s>>>(P, cfg.grid);
+    return cudaGetLastError();
+  }
+  ForceBand whole{0, P.ntot, 0};
+  const ForceBand *bands = cfg.nbands > 0 ? cfg.band : &whole;
+  const int nb = cfg.nbands > 0 ? cfg.nbands : 1;
+  for (int k = 0; k < nb; ++k) {
+    const ForceBand &b = bands[k];
+    if (single) {
+      if (half)
+        launch_variant<true, true>(b.variant, P, b.slot0, b.slot1, s);
+      else
+        launch_variant<true, false>(b.variant, P, b.slot0, b.slot1, s);
+    } else {
+      if (half)
+        launch_variant<false, true>(b.variant, P, b.slot0, b.slot1, s);
+      else
+        launch_variant<false, false>(b.variant, P, b.slot0, b.slot1, s);
+    }
+  }
+  return cudaGetLastError();
+}
+
+// ============================================================ tuning table
+// Process-wide map from density band to direct-kernel variant, one per
+// stencil.  Bands are given by increasing upper bounds of rho (particles per
+// rc^3); densities above the last bound use the last band.
+namespace {
+struct Tuning {
+  std::vector<double> upper;
+  std::vector<int> variant;
+};
+std::mutex g_tune_mu;
+Tuning g_tune[2] = {{{1e30}, {0}}, {{1e30}, {0}}};
+}  // namespace
+
+int tuning_set(int stencil, int n, const double *upper, const int *variant) {
+  if (stencil < 0 || stencil > 1 || n < 1 || n > kMaxBands) return -1;
+  for (int k = 0; k < n; ++k) {
+    if (variant[k] < 0 || variant[k] >= kNumForceVariants) return -1;
+    if (k > 0 && !(upper[k] > upper[k - 1])) return -1;
+  }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[stencil].upper.assign(upper, upper + n);
+  g_tune[stencil].variant.assign(variant, variant + n);
+  return 0;
+}
+
+int tuning_get(int stencil, int max, double *upper, int *variant) {
+  if (stencil < 0 || stencil > 1) return -1;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const Tuning &t = g_tune[stencil];
+  const int n = (int)t.upper.size();
+  for (int k = 0; k < n && k < max; ++k) {
+    if (upper) upper[k] = t.upper[k];
+    if (variant) variant[k] = t.variant[k];
+  }
+  return n;
+}
+
+int tuned_band(int stencil, double rho) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const Tuning &t = g_tune[stencil == 1 ? 1 : 0];
+  for (size_t k = 0; k < t.upper.size(); ++k)
+    if (rho <= t.upper[k]) return (int)k;
+  return (int)t.upper.size() - 1;
+}
+
+int tuned_variant(int stencil, double rho) {
+  const int band = tuned_band(stencil, rho);
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  return g_tune[stencil == 1 ? 1 : 0].variant[band];
+}
+
+}  // namespace dpd

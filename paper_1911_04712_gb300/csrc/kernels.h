@@ -40,13 +40,43 @@ struct TileGrid {
   int stage_cap;  // staged particles per block (positions + velocities)
 };
 
+// A contiguous slot range whose force kernel uses one variant.
+struct ForceBand {
+  int slot0, slot1, variant;
+};
+constexpr int kMaxBands = 8;
+constexpr int kNumForceVariants = 7;
+
 // How a step is launched.
 struct StepConfig {
   int stencil = 0;       // 0 full, 1 half
   bool tiles = false;    // full stencil: staged tiles (true) or one thread per particle
   TileGrid grid{};
+  int nbands = 0;        // 0: one band over every slot with variant 0
+  ForceBand band[kMaxBands]{};
 };
 size_t tile_smem_bytes(int stage_cap);
+cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s);
+
+// Direct force-kernel variants (threads per block, pair-list capacity).
+int force_variant_info(int v, int *threads, int *cap);
+// Process-wide tuning table: density band -> variant, per stencil.
+int tuning_set(int stencil, int n, const double *upper, const int *variant);
+int tuning_get(int stencil, int max, double *upper, int *variant);
+int tuned_band(int stencil, double rho);
+int tuned_variant(int stencil, double rho);
+
+#ifdef __CUDACC__
+// Box constants: the kernel parameter copy for a single box, else from memory.
+template <bool SINGLE>
+__device__ __forceinline__ BoxDev box_of(const Packed &P, int b) {
+  if constexpr (SINGLE) {
+    return P.single;
+  } else {
+    return P.boxes[b];
+  }
+}
+#endif
 
 struct StatsWork {  // one block of the statistics reduction
   int box, begin, end, pad;

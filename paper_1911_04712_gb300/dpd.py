@@ -22,7 +22,7 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_STATE, ERR_NUMERIC, ERR_TIMEOUT, ERR_BUSY 
 WHERE_HOST, WHERE_DEVICE = 0, 1
 PARAM_KEXP, PARAM_MASS, PARAM_BODYFORCE, PARAM_POISEUILLE_F = 1, 2, 3, 4
 PARAM_FLOW_AXIS, PARAM_GRAD_AXIS, PARAM_STENCIL = 5, 6, 7
-PARAM_FORCE_TILES, PARAM_TILE_CELLS, PARAM_STAGE_CAP = 8, 9, 10
+PARAM_FORCE_TILES, PARAM_TILE_CELLS, PARAM_STAGE_CAP, PARAM_FORCE_VARIANT = 8, 9, 10, 11
 STENCIL_FULL, STENCIL_HALF = 0, 1
 NUM_STAGES, KERNELS_PER_STEP = 5, 7
 STAGE_NAMES = ("integrate_bin", "scan", "bin_keys", "bin_scatter", "force")

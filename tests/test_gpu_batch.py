@@ -1,0 +1,136 @@
+"""Batched form: many uneven boxes in one packed set, against each box alone
+and against the oracle."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_04712_gb300.workloads import box_mix, uniform_box_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_1911_04712_gb300 import build
+    build.build()
+    import paper_1911_04712_gb300.batch as B
+    import paper_1911_04712_gb300.dpd as D
+    return D, B
+
+
+def _mix(nbox=10, seed=3):
+    specs = box_mix(nbox, master_seed=seed, L_range=(3, 9))
+    states = [uniform_box_state(s.L, rho=s.rho, kT=s.kT, seed=100 + k) for k, s in enumerate(specs)]
+    return specs, states
+
+
+def _alone(D, s, x, v, nsteps, stencil=0):
+    box = D.Box(s.L, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed,
+                stencil=stencil)
+    box.set_state(x, v)
+    box.step(nsteps)
+    out = box.get_state()
+    f = box.get_forces()
+    box.close()
+    return out, f
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_batch_equals_each_box_alone(mods, stencil):
+    D, B = mods
+    specs, states = _mix()
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
+             for s, st in zip(specs, states)]
+    bt = B.Batch(descs, stencil=stencil)
+    for k, (x, v) in enumerate(states):
+        bt.set_state(k, x, v)
+    nst = 45                                    # one 32-step graph + 13 direct steps
+    bt.step(nst)
+    stats = bt.stats()
+    for k, (s, (x, v)) in enumerate(zip(specs, states)):
+        (xa, va), fa = _alone(D, s, x, v, nst, stencil)
+        xb, vb = bt.get_state(k)
+        fb = bt.get_forces(k)
+        if stencil == 0:
+            assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb), k
+        else:   # atomics: same up to summation order
+            d = xb.astype(np.float64) - xa
+            d -= s.L * np.round(d / s.L)
+            assert np.abs(d).max() < 1e-3, k
+        assert stats[k]["step"] == nst and stats[k]["n"] == len(x)
+
+
+def test_batch_boxes_match_oracle(mods):
+    D, B = mods
+    specs, states = _mix(6, seed=4)
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
+             for s, st in zip(specs, states)]
+    bt = B.Batch(descs)
+    for k, (x, v) in enumerate(states):
+        bt.set_state(k, x, v)
+    f0 = [bt.get_forces(k) for k in range(len(specs))]
+    bt.step(40)
+    for k, (s, (x, v)) in enumerate(zip(specs, states)):
+        p = O.Params(L=(s.L,) * 3, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed)
+        fr, _ = O.forces(p, x, v, 0)
+        rms = math.sqrt((fr ** 2).sum(1).mean())
+        assert np.abs(f0[k] - fr).max() <= 1e-5 * rms
+        st = O.State(p, x, v)
+        st.run(40)
+        xb, _ = bt.get_state(k)
+        d = xb.astype(np.float64) - st.x
+        d -= s.L * np.round(d / s.L)
+        assert np.abs(d).max() < 1e-3
+
+
+def test_batch_step_limits_freeze_boxes(mods):
+    D, B = mods
+    x1, v1 = uniform_box_state(4.0, rho=3, seed=1)
+    x2, v2 = uniform_box_state(5.0, rho=4, seed=2)
+    descs = [B.make_desc(4.0, len(x1), seed=1, steps=10), B.make_desc(5.0, len(x2), seed=2)]
+    bt = B.Batch(descs)
+    bt.set_state(0, x1, v1)
+    bt.set_state(1, x2, v2)
+    bt.step(25)
+    st = bt.stats()
+    assert st[0]["step"] == 10 and st[1]["step"] == 25
+    (xa, va), _ = _alone(D, type("S", (), dict(L=4.0, a=25.0, gamma=4.5, kT=1.0, dt=0.005,
+                                               seed=1))(), x1, v1, 10)
+    xb, vb = bt.get_state(0)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_batch_rejects_bad_descs_and_unloaded_boxes(mods):
+    D, B = mods
+    with pytest.raises(D.DPDError) as ei:
+        B.Batch([B.make_desc(4.0, 10), B.make_desc(2.0, 10)])
+    assert "box 1" in str(ei.value)
+    bt = B.Batch([B.make_desc(4.0, 10), B.make_desc(4.0, 10)])
+    x, v = uniform_box_state(4.0, n=10, seed=0)
+    bt.set_state(0, x, v)
+    with pytest.raises(D.DPDError) as ei:
+        bt.step(1)
+    assert ei.value.code == D.ERR_STATE
+
+
+def test_tuning_table_roundtrip_and_variants_agree(mods):
+    D, B = mods
+    up0, var0 = B.tuning_get(0)
+    try:
+        B.tuning_set(0, [3.5, 4.5, 1e9], [1, 3, 5])
+        assert B.tuning_get(0) == ([3.5, 4.5, 1e9], [1, 3, 5])
+        x, v = uniform_box_state(6.0, rho=3, seed=5)
+        outs = []
+        for variant in range(B.NUM_FORCE_VARIANTS):
+            box = D.Box(6.0, seed=5)
+            box.set_param(D.PARAM_FORCE_VARIANT, variant)
+            box.set_state(x, v)
+            box.step(20)
+            outs.append(box.get_state()[0])
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+    finally:
+        B.tuning_set(0, up0, var0)
