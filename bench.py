@@ -243,6 +243,46 @@ def run_batched(args, stream, world, rank):
             "gpu_launches_per_step": dpd.KERNELS_PER_STEP}
 
 
+def run_served(args):
+    """Prefix of the served request stream: Poisson arrivals submitted in real
+    time to one continuous-batching queue under a 120 GB HBM budget."""
+    import paper_1911_04712_gb300.serve as S
+    from paper_1911_04712_gb300.workloads import request_stream
+
+    reqs = request_stream(args.requests, rate=args.rate, master_seed=args.seed)
+    q = S.Queue(int(120e9), chunk_steps=100, sample_every=20, nbins=16, policy=S.POLICY_FIFO)
+    tickets = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        delay = t0 + r.t_arrival - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(q.submit(S.make_request(r.L, rho=r.rho, a=r.a, gamma=r.gamma, kT=r.kT,
+                                               dt=r.dt, seed=r.seed, steps=r.steps)))
+    q.wait_all(3600)
+    wall = time.perf_counter() - t0
+    res = [q.result(t) for t in tickets]
+    st = q.stats()
+    q.close()
+    lat = sorted(x["latency"] for x in res)
+    work = sum(x["n"] * x["steps"] for x in res)
+    span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+    kt_err = [abs(x["kT_mean"] / r.kT - 1) for x, r in zip(res, reqs)]
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(round(p / 100 * (len(lat) - 1))))]
+
+    return {"workload": f"first {len(reqs)} requests of the stream: Poisson {args.rate:g}/s, "
+                        "L~lognormal(median 16, sigma 0.5) in [8,48], rho in {3,5}, "
+                        "a~U[10,80], gamma~U[2,8], kT~U[0.5,2], steps~U{1000..20000}",
+            "requests": len(res), "failed": sum(1 for x in res if x["status"] != 0),
+            "value": work / span, "unit": UNIT, "particle_steps": work,
+            "p50_latency_s": pct(50), "p99_latency_s": pct(99), "max_latency_s": lat[-1],
+            "wall_s": wall, "gpu_busy_s": st["busy_seconds"],
+            "policy": "first come first served, admission at 100-step chunk boundaries",
+            "kT_mean_rel_err_median": statistics.median(kt_err)}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -360,6 +400,10 @@ def run_native(args):
             dist.all_reduce(t)                 # boxes are sharded: aggregate rates add
             batched["value"], batched["one_box_at_a_time"]["value"] = float(t[0]), float(t[1])
 
+    served = None
+    if not args.no_served and rank == 0:
+        served = run_served(args)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.cpu_L, rho, args.cpu_steps)
@@ -386,6 +430,7 @@ def run_native(args):
             "e2e": e2e,
             "cpu_baseline": base,
             "batched": batched,
+            "served": served,
         }
         print(json.dumps(out), flush=True)
     box.close()
@@ -413,6 +458,9 @@ def main():
     ap.add_argument("--ref-L", type=float, default=32.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--nbox", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--no-e2e", action="store_true")

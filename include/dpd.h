@@ -247,6 +247,77 @@ DPD_API int dpd_batch_get_stats(dpd_batch *b, dpd_stats *out);
 DPD_API int dpd_batch_profile_steps(dpd_batch *b, int64_t nsteps, double *stage_ms);
 DPD_API int dpd_batch_num_boxes(const dpd_batch *b);
 
+/* ================================================================ serving */
+/* A queue admits independent DPD runs as they arrive and runs them on one
+ * GPU with continuous batching: a worker thread steps the resident runs
+ * together (one packed batch) in chunks; between chunks it returns the runs
+ * that reached their step count and admits waiting ones while an HBM
+ * budget and a resident-run limit allow.  Each run starts from an initial
+ * state drawn on the device from its seed (uniform positions, Maxwellian
+ * velocities, zero total momentum) and is stepped and sampled at its own
+ * step indices, so its result does not depend on the other runs. */
+typedef struct dpd_queue dpd_queue;
+
+typedef struct {
+    int64_t max_boxes;       /* resident runs at most (0: 4096) */
+    int64_t chunk_steps;     /* steps between admission points (0: 100) */
+    int64_t sample_every;    /* statistics sample interval in steps (0: 20) */
+    int nbins;               /* velocity-profile slabs, 1..64 (0: 16) */
+    int policy;              /* admission order: 0 first come first served, 1 smallest N x steps */
+    int stencil;             /* DPD_STENCIL_FULL or DPD_STENCIL_HALF */
+    int pad_;
+    double chunk_timeout_s;  /* a chunk not finished after this long fails the queue (0: 600) */
+} dpd_queue_opts;
+
+typedef struct {
+    double box[3];
+    double rho;              /* number density; used when n <= 0 (n = round(rho V)) */
+    int64_t n;
+    double a, gamma, kT, rc, dt;
+    uint64_t seed;           /* noise key and initial-state seed */
+    int64_t steps;           /* steps to run (> 0) */
+    double body_force;       /* 0: none */
+    int body_mode;           /* 1 constant, 2 periodic Poiseuille (Sec. 4.2) */
+    int flow_axis, grad_axis;
+    int pad_;
+} dpd_request;
+
+typedef struct {
+    int status;              /* DPD_OK, or the error that ended the run (DPD_ERR_STATE: cancelled) */
+    int nbins;
+    int64_t n, steps;
+    int64_t samples;         /* statistics samples taken (second half of the run) */
+    double kT_mean;          /* mean of 2 KE / (3 (N - 1)) over the samples */
+    double pressure_mean;    /* mean of N kT / V + virial / (3 V) over the samples */
+    double profile[64];      /* mean flow-axis velocity per slab along the gradient axis */
+    double t_submit, t_admit, t_done;  /* seconds on the queue's clock */
+} dpd_result;
+
+typedef struct {
+    int64_t pending, resident, admitted, completed;
+    uint64_t bytes_in_use;   /* HBM ledger of resident runs */
+    double particle_steps;   /* particle-steps run so far */
+    double busy_seconds;     /* time spent in chunks */
+    double clock_seconds;    /* queue clock now */
+} dpd_queue_stats;
+
+/* Start a queue (and its worker thread) on the current device.  Requests
+ * whose estimated device footprint exceeds hbm_budget_bytes are refused at
+ * submission (DPD_ERR_NOMEM). */
+DPD_API int dpd_queue_create(dpd_queue **out, size_t hbm_budget_bytes, const dpd_queue_opts *opts);
+/* Stop the worker (the current chunk finishes) and release everything. */
+DPD_API int dpd_queue_destroy(dpd_queue *q);
+/* Non-blocking; thread-safe.  *ticket identifies the run. */
+DPD_API int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket);
+DPD_API int dpd_queue_poll(dpd_queue *q, uint64_t ticket, int *done);
+/* DPD_ERR_BUSY until the run has finished. */
+DPD_API int dpd_queue_result(dpd_queue *q, uint64_t ticket, dpd_result *out);
+/* A waiting run finishes at once; a resident one at the next chunk boundary. */
+DPD_API int dpd_queue_cancel(dpd_queue *q, uint64_t ticket);
+/* Wait until no run is waiting or resident; DPD_ERR_TIMEOUT after timeout_s. */
+DPD_API int dpd_queue_wait_all(dpd_queue *q, double timeout_s);
+DPD_API int dpd_queue_get_stats(dpd_queue *q, dpd_queue_stats *out);
+
 /* ------------------------------------------------- forces without allocation */
 /* The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory where they need forces (code inside a host

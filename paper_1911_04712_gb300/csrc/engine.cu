@@ -102,6 +102,8 @@ Engine::~Engine() {
     free_all();
     if (d_.err) cudaFree(d_.err);
     if (d_tiles_) cudaFree(d_tiles_);
+    for (void *q : {(void *)d_wbeg_, (void *)d_from_, (void *)d_acc_, (void *)d_spart_})
+      if (q) cudaFree(q);
     if (cap_) cudaStreamDestroy(cap_);
     if (cur >= 0 && cur != device_) cudaSetDevice(cur);
   }
@@ -379,6 +381,7 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
   ntot_ = (int)ptot;
   ncell_ = (int)ctot;
   st_host_.assign(params.size(), BoxState{0ull, 0ll, 0, 0});
+  from_h_.assign(params.size(), 0ll);
   work_dirty_ = true;
   drop_graph();
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.boxes, boxes_.data(), boxes_.size() * sizeof(BoxDev),
@@ -386,8 +389,10 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.pbase, pbase_.data(), pbase_.size() * sizeof(int),
                                cudaMemcpyHostToDevice, stream_));
   int rc2 = build_tiles();
-  if (rc2) return rc2;
-  return build_bands();
+  if (!rc2) rc2 = build_bands();
+  if (!rc2) rc2 = build_work();
+  if (!rc2 && sample_every_ > 0) rc2 = ensure_sampling_buffers();
+  return rc2;
 }
 
 int Engine::update_params(const std::vector<BoxParams> &params) {
@@ -444,6 +449,12 @@ int Engine::rebuild() {
   for (auto &s : st_host_) s.adv = 1;
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.st, st_host_.data(), st_host_.size() * sizeof(BoxState),
                                cudaMemcpyHostToDevice, stream_));
+  if (sample_every_ > 0) {
+    int rc = ensure_sampling_buffers();
+    if (rc) return rc;
+    DPD_CUDA_TRY(cudaMemcpyAsync(d_from_, from_h_.data(), from_h_.size() * sizeof(long long),
+                                 cudaMemcpyHostToDevice, stream_));
+  }
   DPD_CUDA_TRY(launch_step(packed(), false, false, cfg_, stream_));
   return DPD_OK;
 }
@@ -454,8 +465,12 @@ int Engine::capture_graph() {
   cudaGraph_t g = nullptr;
   DPD_CUDA_TRY(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < graph_chunk && e == cudaSuccess; ++k)
+  for (int k = 0; k < graph_chunk && e == cudaSuccess; ++k) {
     e = launch_step(P, true, true, cfg_, cap_);
+    if (e == cudaSuccess && sample_every_ > 0)
+      e = launch_sample(P, d_.work, (int)work_.size(), d_wbeg_, d_from_, sample_every_, nbins_,
+                        d_spart_, d_acc_, cap_);
+  }
   cudaError_t e2 = cudaStreamEndCapture(cap_, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -499,7 +514,11 @@ int Engine::step(int64_t nsteps) {
     }
   }
   const Packed P = packed();
-  for (int64_t k = 0; k < left; ++k) DPD_CUDA_TRY(launch_step(P, true, true, cfg_, stream_));
+  for (int64_t k = 0; k < left; ++k) {
+    DPD_CUDA_TRY(launch_step(P, true, true, cfg_, stream_));
+    int rc = launch_extra(P, stream_);
+    if (rc) return rc;
+  }
   for (auto &s : st_host_) {
     const int64_t k = std::min<int64_t>(s.remaining, nsteps);
     s.step += (unsigned long long)k;
@@ -584,32 +603,50 @@ int Engine::gather(int box, float *pos, float *vel, float *frc, bool device_ptr)
   return DPD_OK;
 }
 
-int Engine::box_sums(std::vector<double> &sums) {
+int Engine::build_work() {
   const int nb = nbox();
   constexpr int kChunk = 32768;
+  work_.clear();
+  wbeg_.assign(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    wbeg_[b] = (int)work_.size();
+    const int s0 = pbase_[b], s1 = pbase_[b + 1];
+    if (s1 == s0) {
+      work_.push_back(StatsWork{b, s0, s0, 0});
+      continue;
+    }
+    for (int q = s0; q < s1; q += kChunk) work_.push_back(StatsWork{b, q, std::min(q + kChunk, s1), 0});
+  }
+  wbeg_[nb] = (int)work_.size();
+  if (work_.size() > d_.capW) {
+    if (d_.work) cudaFree(d_.work);
+    if (d_.part) cudaFree(d_.part);
+    d_.work = nullptr;
+    d_.part = nullptr;
+    const size_t cap = work_.size() * 2;
+    DPD_CUDA_TRY(cudaMalloc(&d_.work, cap * sizeof(StatsWork)));
+    DPD_CUDA_TRY(cudaMalloc(&d_.part, cap * kStatsFields * sizeof(double)));
+    d_.capW = cap;
+  }
+  if (wbeg_.size() > cap_wbeg_) {
+    if (d_wbeg_) cudaFree(d_wbeg_);
+    d_wbeg_ = nullptr;
+    DPD_CUDA_TRY(cudaMalloc(&d_wbeg_, wbeg_.size() * 2 * sizeof(int)));
+    cap_wbeg_ = wbeg_.size() * 2;
+  }
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_.work, work_.data(), work_.size() * sizeof(StatsWork),
+                               cudaMemcpyHostToDevice, stream_));
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_wbeg_, wbeg_.data(), wbeg_.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, stream_));
+  work_dirty_ = false;
+  return DPD_OK;
+}
+
+int Engine::box_sums(std::vector<double> &sums) {
+  const int nb = nbox();
   if (work_dirty_) {
-    work_.clear();
-    for (int b = 0; b < nb; ++b) {
-      const int s0 = pbase_[b], s1 = pbase_[b + 1];
-      if (s1 == s0) {
-        work_.push_back(StatsWork{b, s0, s0, 0});
-        continue;
-      }
-      for (int s = s0; s < s1; s += kChunk) work_.push_back(StatsWork{b, s, std::min(s + kChunk, s1), 0});
-    }
-    if (work_.size() > d_.capW) {
-      if (d_.work) cudaFree(d_.work);
-      if (d_.part) cudaFree(d_.part);
-      d_.work = nullptr;
-      d_.part = nullptr;
-      const size_t cap = work_.size() * 2;
-      DPD_CUDA_TRY(cudaMalloc(&d_.work, cap * sizeof(StatsWork)));
-      DPD_CUDA_TRY(cudaMalloc(&d_.part, cap * kStatsFields * sizeof(double)));
-      d_.capW = cap;
-    }
-    DPD_CUDA_TRY(cudaMemcpyAsync(d_.work, work_.data(), work_.size() * sizeof(StatsWork),
-                                 cudaMemcpyHostToDevice, stream_));
-    work_dirty_ = false;
+    int rc = build_work();
+    if (rc) return rc;
   }
   std::vector<double> part(work_.size() * kStatsFields);
   DPD_CUDA_TRY(launch_stats(packed(), d_.work, (int)work_.size(), d_.part, stream_));
@@ -620,6 +657,188 @@ int Engine::box_sums(std::vector<double> &sums) {
   for (size_t w = 0; w < work_.size(); ++w)
     for (int k = 0; k < kStatsFields; ++k)
       sums[(size_t)work_[w].box * kStatsFields + k] += part[w * kStatsFields + k];
+  return DPD_OK;
+}
+
+// ------------------------------------------------------------ served form
+int Engine::enable_sampling(int every, int nbins) {
+  if (every < 0 || nbins < 0 || nbins > 64)
+    return set_error(DPD_ERR_ARG, "sampling: every >= 0, 0 <= nbins <= 64");
+  sample_every_ = every;
+  nbins_ = nbins;
+  drop_graph();
+  if (!boxes_.empty() && every > 0) return ensure_sampling_buffers();
+  return DPD_OK;
+}
+
+int Engine::ensure_sampling_buffers() {
+  const size_t nb = boxes_.size(), f = (size_t)sample_fields();
+  if (nb > cap_from_) {
+    if (d_from_) cudaFree(d_from_);
+    d_from_ = nullptr;
+    DPD_CUDA_TRY(cudaMalloc(&d_from_, nb * 2 * sizeof(long long)));
+    cap_from_ = nb * 2;
+    drop_graph();
+  }
+  if (nb * f > cap_acc_) {
+    std::vector<double> keep;
+    if (d_acc_) cudaFree(d_acc_);
+    d_acc_ = nullptr;
+    DPD_CUDA_TRY(cudaMalloc(&d_acc_, nb * f * 2 * sizeof(double)));
+    DPD_CUDA_TRY(cudaMemsetAsync(d_acc_, 0, nb * f * 2 * sizeof(double), stream_));
+    cap_acc_ = nb * f * 2;
+    drop_graph();
+  }
+  if (work_.size() * f > cap_spart_) {
+    if (d_spart_) cudaFree(d_spart_);
+    d_spart_ = nullptr;
+    DPD_CUDA_TRY(cudaMalloc(&d_spart_, work_.size() * f * 2 * sizeof(double)));
+    cap_spart_ = work_.size() * f * 2;
+    drop_graph();
+  }
+  return DPD_OK;
+}
+
+int Engine::launch_extra(const Packed &P, cudaStream_t s) {
+  if (sample_every_ <= 0) return DPD_OK;
+  DPD_CUDA_TRY(launch_sample(P, d_.work, (int)work_.size(), d_wbeg_, d_from_, sample_every_,
+                             nbins_, d_spart_, d_acc_, s));
+  return DPD_OK;
+}
+
+int Engine::zero_acc(int box) {
+  if (box < 0 || box >= nbox() || !d_acc_) return set_error(DPD_ERR_ARG, "no accumulator");
+  const size_t f = (size_t)sample_fields();
+  DPD_CUDA_TRY(cudaMemsetAsync(d_acc_ + (size_t)box * f, 0, f * sizeof(double), stream_));
+  return DPD_OK;
+}
+
+int Engine::read_acc(int box, double *out) {
+  if (box < 0 || box >= nbox() || !d_acc_) return set_error(DPD_ERR_ARG, "no accumulator");
+  const size_t f = (size_t)sample_fields();
+  DPD_CUDA_TRY(cudaMemcpyAsync(out, d_acc_ + (size_t)box * f, f * sizeof(double),
+                               cudaMemcpyDeviceToHost, stream_));
+  DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  return DPD_OK;
+}
+
+int Engine::init_box(int box, uint64_t seed) {
+  if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
+  const BoxParams &bp = params_[box];
+  const float vscale = (float)std::sqrt(bp.kT / bp.mass);
+  DPD_CUDA_TRY(launch_init_box(packed(), pbase_[box], pbase_[box + 1] - pbase_[box],
+                               (float)bp.L[0], (float)bp.L[1], (float)bp.L[2], vscale, seed,
+                               stream_));
+  return DPD_OK;
+}
+
+int Engine::repack(const std::vector<BoxParams> &params, const std::vector<int64_t> &np,
+                   const std::vector<int> &src) {
+  if (params.size() != np.size() || src.size() != np.size() || params.empty())
+    return set_error(DPD_ERR_ARG, "repack: inconsistent sizes");
+  const std::vector<int> old_pbase = pbase_;
+  const std::vector<BoxState> old_st = st_host_;
+  const std::vector<long long> old_from = from_h_;
+  const int old_ntot = ntot_;
+  const size_t f = (size_t)sample_fields();
+  std::vector<double> old_acc;
+  if (sample_every_ > 0 && d_acc_ && !boxes_.empty()) {
+    old_acc.resize(boxes_.size() * f);
+    DPD_CUDA_TRY(cudaMemcpyAsync(old_acc.data(), d_acc_, old_acc.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, stream_));
+    DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  }
+  std::vector<int> newbase(np.size() + 1, 0), src0(np.size(), -1);
+  for (size_t k = 0; k < np.size(); ++k) {
+    newbase[k + 1] = newbase[k] + (int)np[k];
+    if (src[k] >= 0) {
+      if (src[k] >= (int)old_st.size() || old_pbase[src[k] + 1] - old_pbase[src[k]] != np[k])
+        return set_error(DPD_ERR_ARG, "repack: box %zu does not match its source", k);
+      src0[k] = old_pbase[src[k]];
+    }
+  }
+  const int new_ntot = newbase.back();
+  int *d_nb = nullptr, *d_src = nullptr;
+  DPD_CUDA_TRY(cudaMalloc(&d_nb, newbase.size() * sizeof(int)));
+  DPD_CUDA_TRY(cudaMalloc(&d_src, src0.size() * sizeof(int)));
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_nb, newbase.data(), newbase.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, stream_));
+  DPD_CUDA_TRY(cudaMemcpyAsync(d_src, src0.data(), src0.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, stream_));
+  cudaError_t e = cudaSuccess;
+  if ((size_t)new_ntot > d_.capP) {
+    // grow: gather straight from the old arrays into new ones
+    const size_t cap = std::max((size_t)new_ntot, d_.capP + d_.capP / 4);
+    float4 *np_ = nullptr, *nv_ = nullptr;
+    e = cudaMalloc(&np_, cap * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&nv_, cap * sizeof(float4));
+    if (e == cudaSuccess)
+      e = launch_repack(d_.pos, d_.vel, np_, nv_, d_nb, d_src, (int)np.size(), new_ntot, stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    if (e != cudaSuccess) {
+      if (np_) cudaFree(np_);
+      if (nv_) cudaFree(nv_);
+      cudaFree(d_nb);
+      cudaFree(d_src);
+      return set_error(e == cudaErrorMemoryAllocation ? DPD_ERR_NOMEM : DPD_ERR_CUDA,
+                       "repack: %s", cudaGetErrorString(e));
+    }
+    float4 *keep_pos = np_, *keep_vel = nv_;
+    drop_graph();
+    void *olds[] = {d_.pos, d_.vel, d_.frc, d_.pos2, d_.vel2, d_.cellOf, d_.slotIn, d_.keyTmp};
+    for (void *q : olds)
+      if (q) cudaFree(q);
+    d_.pos = d_.vel = d_.frc = d_.pos2 = d_.vel2 = nullptr;
+    d_.cellOf = d_.slotIn = d_.keyTmp = nullptr;
+    d_.capP = 0;
+    int rc = reserve((size_t)new_ntot, 0, 0);   // allocates the rest at a new capacity
+    if (rc) {
+      cudaFree(keep_pos);
+      cudaFree(keep_vel);
+      cudaFree(d_nb);
+      cudaFree(d_src);
+      return rc;
+    }
+    cudaFree(d_.pos);
+    cudaFree(d_.vel);
+    d_.pos = keep_pos;
+    d_.vel = keep_vel;
+  } else {
+    e = cudaMemcpyAsync(d_.pos2, d_.pos, (size_t)old_ntot * sizeof(float4),
+                        cudaMemcpyDeviceToDevice, stream_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_.vel2, d_.vel, (size_t)old_ntot * sizeof(float4),
+                          cudaMemcpyDeviceToDevice, stream_);
+    if (e == cudaSuccess)
+      e = launch_repack(d_.pos2, d_.vel2, d_.pos, d_.vel, d_nb, d_src, (int)np.size(), new_ntot,
+                        stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    if (e != cudaSuccess) {
+      cudaFree(d_nb);
+      cudaFree(d_src);
+      return set_error(DPD_ERR_CUDA, "repack: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaFree(d_nb);
+  cudaFree(d_src);
+  int rc = layout(params, np);
+  if (rc) return rc;
+  for (size_t k = 0; k < np.size(); ++k) {
+    if (src[k] >= 0) {
+      st_host_[k] = old_st[src[k]];
+      from_h_[k] = old_from[src[k]];
+    }
+  }
+  if (sample_every_ > 0) {
+    std::vector<double> acc(np.size() * f, 0.0);
+    for (size_t k = 0; k < np.size(); ++k)
+      if (src[k] >= 0 && !old_acc.empty())
+        std::copy(old_acc.begin() + (size_t)src[k] * f, old_acc.begin() + (size_t)(src[k] + 1) * f,
+                  acc.begin() + k * f);
+    DPD_CUDA_TRY(cudaMemcpyAsync(d_acc_, acc.data(), acc.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, stream_));
+    DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  }
   return DPD_OK;
 }
 

@@ -103,6 +103,25 @@ class Engine {
   int check_error();                // reads and clears the device error word
 
   int gather(int box, float *pos, float *vel, float *frc, bool device_ptr);
+
+  // ---- served form
+  // Statistics sampling every `every` box steps into per-box FP64
+  // accumulators {samples, sum v^2, sum frc.w, slab sums, slab counts};
+  // every = 0 turns it off.
+  int enable_sampling(int every, int nbins);
+  int sample_fields() const { return 3 + 2 * nbins_; }
+  // Boxes sample only at steps > from (host mirror; uploaded at rebuild).
+  void set_sample_from(int box, long long from) { from_h_[box] = from; }
+  int zero_acc(int box);
+  int read_acc(int box, double *out);  // synchronises the stream
+  // Draw a box's initial state on the device (uniform positions, Maxwellian
+  // velocities of variance kT/m, zero mean momentum).
+  int init_box(int box, uint64_t seed);
+  // New packing: box k of `params` is old box src[k] (its particles, step
+  // state and accumulators are kept) or new (src[k] < 0, to be loaded or
+  // initialised).  Call rebuild() before stepping.
+  int repack(const std::vector<BoxParams> &params, const std::vector<int64_t> &np,
+             const std::vector<int> &src);
   // FP64 partial sums per box: {sum v (3), sum v^2, sum frc.w, count}.
   int box_sums(std::vector<double> &sums);
 
@@ -141,7 +160,18 @@ class Engine {
   int ntot_ = 0, ncell_ = 0;
   DeviceArrays d_;
   std::vector<StatsWork> work_;
+  std::vector<int> wbeg_;            // first work item of each box (nbox + 1)
+  int *d_wbeg_ = nullptr;
+  size_t cap_wbeg_ = 0;
   bool work_dirty_ = true;
+  int build_work();
+  int sample_every_ = 0, nbins_ = 0;
+  std::vector<long long> from_h_;
+  long long *d_from_ = nullptr;
+  double *d_acc_ = nullptr, *d_spart_ = nullptr;
+  size_t cap_from_ = 0, cap_acc_ = 0, cap_spart_ = 0;
+  int ensure_sampling_buffers();
+  int launch_extra(const Packed &P, cudaStream_t s);
   cudaGraphExec_t graph_ = nullptr;
 };
 

@@ -328,6 +328,196 @@ __global__ void k_debug_rng(const uint32_t *__restrict__ lo, const uint32_t *__r
   if (xi) xi[k] = __fmul_rn(noise_int(u), kSqrt3Scale);
 }
 
+// ------------------------------------------------------ served-form kernels
+// Initial state of a new box drawn on the device from its seed: positions
+// uniform in [0, L), velocities Maxwellian (Box-Muller) with variance kT/m.
+// Philox-4x32-10 with key (seed lo, seed hi ^ 0x5EED0001) on counters
+// (id, 0, 0, 0) and (id, 1, 0, 0); this only samples an initial condition.
+__device__ __forceinline__ void philox4(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1,
+                                        uint32_t out[4]) {
+  uint32_t c2 = 0u, c3 = 0u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+__device__ __forceinline__ float unit_open(uint32_t u) {  // (0, 1)
+  return ((float)(u >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+__global__ void k_init_box(Packed P, int slot0, int n, float Lx, float Ly, float Lz, float vscale,
+                           uint32_t seed_lo, uint32_t seed_hi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t a[4], b[4];
+  philox4((uint32_t)i, 0u, seed_lo, seed_hi ^ 0x5EED0001u, a);
+  philox4((uint32_t)i, 1u, seed_lo, seed_hi ^ 0x5EED0001u, b);
+  float x = unit_open(a[0]) * Lx, y = unit_open(a[1]) * Ly, z = unit_open(a[2]) * Lz;
+  x = x < Lx ? x : 0.f;
+  y = y < Ly ? y : 0.f;
+  z = z < Lz ? z : 0.f;
+  const float r1 = sqrtf(-2.0f * logf(unit_open(b[0])));
+  const float r2 = sqrtf(-2.0f * logf(unit_open(b[2])));
+  float s1, c1, s2, c2;
+  sincospif(2.0f * unit_open(b[1]), &s1, &c1);
+  sincospif(2.0f * unit_open(b[3]), &s2, &c2);
+  P.pos[slot0 + i] = make_float4(x, y, z, __int_as_float(i));
+  P.vel[slot0 + i] = make_float4(vscale * r1 * c1, vscale * r1 * s1, vscale * r2 * c2, 0.f);
+}
+
+// Remove the mean velocity of one box: one block sums in a fixed order (FP64),
+// then every thread subtracts.
+__global__ void __launch_bounds__(1024) k_zero_momentum(Packed P, int slot0, int n) {
+  __shared__ double red[3][32];
+  __shared__ float mean[3];
+  double s[3] = {0, 0, 0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float4 v = P.vel[slot0 + i];
+    s[0] += v.x;
+    s[1] += v.y;
+    s[2] += v.z;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double t = s[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) red[k][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[threadIdx.x][w];
+    mean[threadIdx.x] = (float)(n > 0 ? t / n : 0.0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float4 v = P.vel[slot0 + i];
+    v.x -= mean[0];
+    v.y -= mean[1];
+    v.z -= mean[2];
+    P.vel[slot0 + i] = v;
+  }
+}
+
+// Move surviving boxes to their new slot ranges: new slot q of new box b
+// takes old slot src0[b] + (q - newbase[b]) (src0 < 0: a new box, skipped).
+__global__ void k_repack(const float4 *__restrict__ opos, const float4 *__restrict__ ovel,
+                         float4 *__restrict__ npos, float4 *__restrict__ nvel,
+                         const int *__restrict__ newbase, const int *__restrict__ src0, int nbox,
+                         int ntot) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ntot) return;
+  const int b = find_box(newbase, nbox, q);
+  const int s0 = src0[b];
+  if (s0 < 0) return;
+  const int src = s0 + (q - newbase[b]);
+  npos[q] = opos[src];
+  nvel[q] = ovel[src];
+}
+
+// Statistics sample of every box whose step is a multiple of `every` and
+// past its window start: per work item FP64 partials of sum v^2, sum r.F^C
+// (frc.w, each pair counted twice) and per-slab sums of the flow-axis
+// velocity with their counts.
+__global__ void __launch_bounds__(256) k_sample(Packed P, const StatsWork *__restrict__ work,
+                                                const long long *__restrict__ from, int every,
+                                                int nbins, double *__restrict__ part) {
+  extern __shared__ double sbin[];  // 2 * nbins: sums then counts
+  const StatsWork w = work[blockIdx.x];
+  const BoxState S = P.st[w.box];
+  const int fields = 3 + 2 * nbins;
+  double *out = part + (size_t)blockIdx.x * fields;
+  const bool take = S.adv && every > 0 && (long long)S.step > from[w.box] &&
+                    (S.step % (unsigned long long)every) == 0ull;
+  if (!take) {
+    if (threadIdx.x == 0) out[0] = 0.0;  // marks "no sample"
+    return;
+  }
+  for (int k = threadIdx.x; k < 2 * nbins; k += blockDim.x) sbin[k] = 0.0;
+  __syncthreads();
+  const BoxDev B = P.boxes[w.box];
+  const float h = S.pending ? B.hdt_m : 0.0f;
+  const float Lg = B.L[B.fb_grad];
+  double v2 = 0.0, vir = 0.0;
+  for (int p = w.begin + threadIdx.x; p < w.end; p += blockDim.x) {
+    const float4 x = P.pos[p];
+    float4 v = P.vel[p];
+    const float4 f = P.frc[p];
+    v.x = fmaf(h, f.x, v.x);
+    v.y = fmaf(h, f.y, v.y);
+    v.z = fmaf(h, f.z, v.z);
+    v2 += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+    vir += (double)f.w;
+    if (nbins > 0) {
+      const float xg = (B.fb_grad == 0) ? x.x : (B.fb_grad == 1) ? x.y : x.z;
+      const float vf = (B.fb_flow == 0) ? v.x : (B.fb_flow == 1) ? v.y : v.z;
+      int bin = (int)(xg / Lg * nbins);
+      bin = min(max(bin, 0), nbins - 1);
+      atomicAdd(&sbin[bin], (double)vf);
+      atomicAdd(&sbin[nbins + bin], 1.0);
+    }
+  }
+  __shared__ double red[2][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+    vir += __shfl_down_sync(0xffffffffu, vir, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = v2;
+    red[1][warp] = vir;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) {
+      a += red[0][q];
+      c += red[1][q];
+    }
+    out[0] = 1.0;
+    out[1] = a;
+    out[2] = c;
+  }
+  for (int k = threadIdx.x; k < 2 * nbins; k += blockDim.x) out[3 + k] = sbin[k];
+}
+
+// Add each box's work-item partials (in work order) to its accumulators:
+// acc[b] = {samples, sum v^2, sum frc.w, slab sums[nbins], slab counts[nbins]}.
+__global__ void k_sample_acc(const StatsWork *__restrict__ work, const int *__restrict__ wbeg,
+                             int nbox, int nbins, const double *__restrict__ part,
+                             double *__restrict__ acc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox) return;
+  const int fields = 3 + 2 * nbins;
+  const int w0 = wbeg[b], w1 = wbeg[b + 1];
+  if (w1 <= w0 || part[(size_t)w0 * fields] == 0.0) return;
+  double *a = acc + (size_t)b * fields;
+  a[0] += 1.0;
+  for (int k = 1; k < fields; ++k) {
+    double s = 0.0;
+    for (int w = w0; w < w1; ++w) s += part[(size_t)w * fields + k];
+    a[k] += s;
+  }
+}
+
 // ================================================================ launchers
 
 cudaError_t launch_load(const Packed &P, int slot0, int n, const float *pos3, const float *vel3,
@@ -403,6 +593,37 @@ cudaError_t launch_debug_rng(const uint32_t *lo, const uint32_t *hi, long long n
   k_debug_rng<<<blocks_for(n, 256), 256, 0, s>>>(lo, hi, n, (uint32_t)step,
                                                  (uint32_t)(step >> 32), (uint32_t)seed,
                                                  (uint32_t)(seed >> 32), out, xi);
+  return cudaGetLastError();
+}
+
+}  // namespace dpd
+
+namespace dpd {
+
+cudaError_t launch_init_box(const Packed &P, int slot0, int n, float Lx, float Ly, float Lz,
+                            float vscale, uint64_t seed, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_init_box<<<blocks_for(n, 256), 256, 0, s>>>(P, slot0, n, Lx, Ly, Lz, vscale, (uint32_t)seed,
+                                                 (uint32_t)(seed >> 32));
+  k_zero_momentum<<<1, 1024, 0, s>>>(P, slot0, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_repack(const float4 *opos, const float4 *ovel, float4 *npos, float4 *nvel,
+                          const int *newbase, const int *src0, int nbox, int ntot,
+                          cudaStream_t s) {
+  if (ntot <= 0) return cudaSuccess;
+  k_repack<<<blocks_for(ntot, 256), 256, 0, s>>>(opos, ovel, npos, nvel, newbase, src0, nbox,
+                                                  ntot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const Packed &P, const StatsWork *work, int nwork, const int *wbeg,
+                          const long long *from, int every, int nbins, double *part, double *acc,
+                          cudaStream_t s) {
+  if (nwork <= 0 || every <= 0) return cudaSuccess;
+  k_sample<<<nwork, 256, 2 * nbins * sizeof(double), s>>>(P, work, from, every, nbins, part);
+  k_sample_acc<<<blocks_for(P.nbox, 128), 128, 0, s>>>(work, wbeg, P.nbox, nbins, part, acc);
   return cudaGetLastError();
 }
 

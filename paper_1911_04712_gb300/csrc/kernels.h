@@ -120,6 +120,18 @@ cudaError_t launch_stats(const Packed &P, const StatsWork *work, int nwork, doub
 cudaError_t launch_gather(const Packed &P, int box, int slot0, int n, float *pos3, float *vel3,
                           float *frc3, cudaStream_t s);
 
+// Served form: device-drawn initial state of a box (uniform positions,
+// Maxwellian velocities with variance vscale^2, zero mean momentum).
+cudaError_t launch_init_box(const Packed &P, int slot0, int n, float Lx, float Ly, float Lz,
+                            float vscale, uint64_t seed, cudaStream_t s);
+// Copy surviving boxes' particles into a new packing.
+cudaError_t launch_repack(const float4 *opos, const float4 *ovel, float4 *npos, float4 *nvel,
+                          const int *newbase, const int *src0, int nbox, int ntot, cudaStream_t s);
+// Statistics sample (boxes whose step is a multiple of `every` past from[b]).
+cudaError_t launch_sample(const Packed &P, const StatsWork *work, int nwork, const int *wbeg,
+                          const long long *from, int every, int nbins, double *part, double *acc,
+                          cudaStream_t s);
+
 cudaError_t launch_debug_rng(const uint32_t *lo, const uint32_t *hi, long long n, uint64_t step,
                              uint64_t seed, uint32_t *out, float *xi, cudaStream_t s);
 
