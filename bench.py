@@ -195,9 +195,11 @@ def run_batched(args, stream, world, rank):
     import paper_1911_04712_gb300.dpd as dpd
     from paper_1911_04712_gb300.workloads import box_mix, uniform_box_state
 
+    from paper_1911_04712_gb300.shard import shard_boxes
     specs = box_mix(args.nbox, master_seed=args.seed)
-    if world > 1:                       # shard boxes over ranks, no collective
-        specs = specs[rank::world]
+    if world > 1:                       # shard boxes over ranks, no data-path collective
+        mine = shard_boxes([s.n * args.batch_steps for s in specs], rank, world)
+        specs = [specs[k] for k in mine]
     states = [uniform_box_state(s.L, rho=s.rho, kT=s.kT, seed=s.seed) for s in specs]
     n_tot = sum(len(x) for x, _ in states)
     descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
@@ -231,11 +233,17 @@ def run_batched(args, stream, world, rank):
     ms_s = e0.elapsed_time(e1)
     for b in boxes:
         b.close()
-    rate_b = n_tot * args.batch_steps / (ms_b / 1000.0)
-    rate_s = n_tot * args.batch_steps / (ms_s / 1000.0)
-    return {"workload": f"box mix: {len(specs)} boxes, L~U{{6..24}}, rho in {{3,4,5}}, "
+    import torch.distributed as tdist
+    from paper_1911_04712_gb300.shard import combine
+    units, sec_b = combine(float(n_tot * args.batch_steps), ms_b / 1000.0, tdist, "cuda")
+    _, sec_s = combine(float(n_tot * args.batch_steps), ms_s / 1000.0, tdist, "cuda")
+    n_all, _ = combine(float(n_tot), 0.0, tdist, "cuda")
+    rate_b = units / sec_b
+    rate_s = units / sec_s
+    n_tot = int(n_all)
+    return {"workload": f"box mix: {args.nbox} boxes, L~U{{6..24}}, rho in {{3,4,5}}, "
                         f"a~U[10,80], gamma~U[2,8], kT~U[0.5,2], dt=0.005",
-            "boxes": len(specs), "particles": n_tot, "steps": args.batch_steps,
+            "boxes": args.nbox, "particles": n_tot, "steps": args.batch_steps,
             "value": rate_b, "unit": UNIT, "ms_per_step": ms_b / args.batch_steps,
             "one_box_at_a_time": {"value": rate_s, "ms_per_step": ms_s / args.batch_steps},
             "speedup_vs_one_at_a_time": rate_b / rate_s,
@@ -243,13 +251,18 @@ def run_batched(args, stream, world, rank):
             "gpu_launches_per_step": dpd.KERNELS_PER_STEP}
 
 
-def run_served(args):
+def run_served(args, rank=0, world=1):
     """Prefix of the served request stream: Poisson arrivals submitted in real
-    time to one continuous-batching queue under a 120 GB HBM budget."""
+    time to one continuous-batching queue per GPU under a 120 GB HBM budget
+    (with N GPUs, requests go round-robin to the ranks' queues)."""
+    import torch.distributed as tdist
+
     import paper_1911_04712_gb300.serve as S
+    from paper_1911_04712_gb300.shard import gather_list, shard_requests
     from paper_1911_04712_gb300.workloads import request_stream
 
     reqs = request_stream(args.requests, rate=args.rate, master_seed=args.seed)
+    reqs = [reqs[k] for k in shard_requests(len(reqs), rank, world)]
     q = S.Queue(int(120e9), chunk_steps=100, sample_every=20, nbins=16, policy=S.POLICY_FIFO)
     tickets = []
     t0 = time.perf_counter()
@@ -264,18 +277,20 @@ def run_served(args):
     res = [q.result(t) for t in tickets]
     st = q.stats()
     q.close()
-    lat = sorted(x["latency"] for x in res)
-    work = sum(x["n"] * x["steps"] for x in res)
-    span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
-    kt_err = [abs(x["kT_mean"] / r.kT - 1) for x, r in zip(res, reqs)]
+    lat = sorted(gather_list([x["latency"] for x in res], tdist))
+    work = sum(gather_list([x["n"] * x["steps"] for x in res], tdist))
+    span = max(gather_list([max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)],
+                           tdist))
+    kt_err = gather_list([abs(x["kT_mean"] / r.kT - 1) for x, r in zip(res, reqs)], tdist)
+    failed = sum(gather_list([sum(1 for x in res if x["status"] != 0)], tdist))
 
     def pct(p):
         return lat[min(len(lat) - 1, int(round(p / 100 * (len(lat) - 1))))]
 
-    return {"workload": f"first {len(reqs)} requests of the stream: Poisson {args.rate:g}/s, "
+    return {"workload": f"first {args.requests} requests of the stream: Poisson {args.rate:g}/s, "
                         "L~lognormal(median 16, sigma 0.5) in [8,48], rho in {3,5}, "
                         "a~U[10,80], gamma~U[2,8], kT~U[0.5,2], steps~U{1000..20000}",
-            "requests": len(res), "failed": sum(1 for x in res if x["status"] != 0),
+            "requests": len(lat), "failed": failed,
             "value": work / span, "unit": UNIT, "particle_steps": work,
             "p50_latency_s": pct(50), "p99_latency_s": pct(99), "max_latency_s": lat[-1],
             "wall_s": wall, "gpu_busy_s": st["busy_seconds"],
@@ -394,15 +409,10 @@ def run_native(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, stream, world, rank)
-        if dist:
-            t = torch.tensor([batched["value"], batched["one_box_at_a_time"]["value"]],
-                             device="cuda", dtype=torch.float64)
-            dist.all_reduce(t)                 # boxes are sharded: aggregate rates add
-            batched["value"], batched["one_box_at_a_time"]["value"] = float(t[0]), float(t[1])
 
     served = None
-    if not args.no_served and rank == 0:
-        served = run_served(args)
+    if not args.no_served:
+        served = run_served(args, rank, world)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -443,7 +453,7 @@ def run_native(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--L", type=float, default=128.0)

@@ -1,0 +1,102 @@
+"""Density sweep with the periodic Poiseuille force (Sec. 4.2): flow along x,
+force -f for y <= L/2 and +f above, f = 0.05, 2000 steps.
+
+* L = 12, rho = 3: the GPU and the oracle start from the same state; their
+  trajectories decorrelate (the dynamics is chaotic) so the time-averaged
+  velocity profiles are compared within their statistical error.
+* L = 48, rho = 3 / 5 / 10 (a = 25 / 15 / 7.5), GPU only: 2000 steps are 10
+  time units, far below the viscous time (L/2)^2 / nu, so away from the two
+  planes where the force switches each half moves as a plug, v_x = -/+ f t
+  (the start-up of the flow); the kinetic temperature stays at kT.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_04712_gb300.workloads import uniform_box_state
+
+pytestmark = pytest.mark.gpu
+F0 = 0.05
+
+
+@pytest.fixture(scope="module")
+def dpd():
+    from paper_1911_04712_gb300 import build
+    build.build()
+    import paper_1911_04712_gb300.dpd as d
+    return d
+
+
+def _profile(x, v, L, nbins):
+    b = np.clip((x[:, 1] / L * nbins).astype(int), 0, nbins - 1)
+    s = np.bincount(b, weights=v[:, 0].astype(np.float64), minlength=nbins)
+    c = np.bincount(b, minlength=nbins)
+    return s / np.maximum(c, 1)
+
+
+def _box(dpd, L, a, seed):
+    box = dpd.Box(L, a=a, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=seed)
+    box.set_param(dpd.PARAM_FLOW_AXIS, 0)
+    box.set_param(dpd.PARAM_GRAD_AXIS, 1)
+    box.set_param(dpd.PARAM_POISEUILLE_F, F0)
+    return box
+
+
+def test_startup_profile_matches_oracle_statistically(dpd):
+    L, nb = 12.0, 6
+    x, v = uniform_box_state(L, rho=3, seed=31)
+    box = _box(dpd, L, 25.0, 31)
+    box.set_state(x, v)
+    p = O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=1.0, dt=0.005, seed=31, fb=F0,
+                 fb_mode=O.FB_POISEUILLE, fb_flow=0, fb_grad=1)
+    st = O.State(p, x, v, mode=O.MODE_CELLS)
+    box.step(1000)
+    st.run(1000)
+    gpu, ref = [], []
+    for _ in range(50):
+        box.step(20)
+        st.run(20)
+        xg, vg = box.get_state()
+        gpu.append(_profile(xg, vg, L, nb))
+        ref.append(_profile(st.x, st.v, L, nb))
+    gpu, ref = np.array(gpu), np.array(ref)
+    n_bin = len(x) / nb
+    # standard error of a time-averaged bin mean: per-sample sqrt(kT / n_bin),
+    # about 10 independent samples in 1000 steps (velocity correlation time ~ 0.5)
+    sigma = np.sqrt(1.0 / n_bin) / np.sqrt(10.0)
+    diff = gpu.mean(0) - ref.mean(0)
+    assert np.all(np.abs(diff) < 5 * np.sqrt(2) * sigma), (diff, sigma)
+    # and both show the driven profile: negative below L/2, positive above
+    for prof in (gpu.mean(0), ref.mean(0)):
+        assert prof[: nb // 2].mean() < -0.1 and prof[nb // 2:].mean() > 0.1
+
+
+@pytest.mark.parametrize("rho,a", [(3, 25.0), (5, 15.0), (10, 7.5)])
+def test_full_size_density_sweep_plug_flow(dpd, rho, a):
+    L, nb, nsteps = 48.0, 24, 2000
+    x, v = uniform_box_state(L, rho=rho, seed=5)
+    box = _box(dpd, L, a, 5)
+    box.set_state(x, v)
+    P0 = box.stats()["momentum"]
+    box.step(nsteps)
+    xg, vg = box.get_state()
+    prof = _profile(xg, vg, L, nb)
+    t = nsteps * 0.005
+    # bins away from the switching planes y = 0 and y = L/2 (shear layers ~ sqrt(nu t))
+    lower = prof[3:nb // 2 - 3]
+    upper = prof[nb // 2 + 3:nb - 3]
+    assert np.all(np.abs(lower + F0 * t) < 0.15 * F0 * t + 0.05), lower
+    assert np.all(np.abs(upper - F0 * t) < 0.15 * F0 * t + 0.05), upper
+    st = box.stats()
+    # temperature of the peculiar velocities (flow profile removed)
+    b = np.clip((xg[:, 1] / L * nb).astype(int), 0, nb - 1)
+    pec = vg.astype(np.float64).copy()
+    pec[:, 0] -= prof[b]
+    kT_pec = (pec ** 2).sum() / (3.0 * (len(xg) - 1))
+    assert abs(kT_pec - 1.0) < 0.03, kT_pec
+    assert st["kT"] > kT_pec        # the stats kT also counts the flow's kinetic energy
+    # the two halves cancel: the net body force is f times a count imbalance of
+    # O(sqrt(N)), so the total momentum stays a small fraction of sum |m v|
+    scale = np.linalg.norm(vg.astype(np.float64), axis=1).sum()
+    assert np.abs(st["momentum"] - P0).max() < 1e-2 * scale
