@@ -31,44 +31,82 @@ constexpr uint32_t kSlotMask = (1u << 26) - 1u;
 constexpr uint32_t kCodeJX = 1u << 26, kCodeIX = 1u << 27, kCodeJY = 1u << 28,
                    kCodeIY = 1u << 29, kCodeJZ = 1u << 30, kCodeIZ = 1u << 31;
 
+// 0 < r2 < rc2 as one unsigned compare of the bit patterns (both are
+// non-negative floats, whose bit patterns order like their values).
+__device__ __forceinline__ bool in_range(float r2, uint32_t rc2_bits_minus_1) {
+  return (__float_as_uint(r2) - 1u) < rc2_bits_minus_1;
+}
+
 // Candidate pass over slots [j0, j1): appends every j with 0 < r_ij^2 < rc^2.
-// The append is branch-free (the slot is written every iteration and kept only
-// on a hit), so the lanes of a warp stay converged.  Returns the slot at which
-// the list became full, or -1 when the range was scanned completely.
+// The append is branch-free (the slot is written every candidate and kept
+// only on a hit), so the lanes of a warp stay converged; two candidates are
+// loaded per iteration.  Needs at least 2 free list entries on entry.
+// Returns the next slot to scan when the list has fewer than 2 free entries,
+// or -1 when the range was scanned completely.
 template <bool JSHIFT, int NT, int CAP>
 __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0, int j1,
                                           float ax, float ay, float az, float jsx, float jsy,
-                                          float jsz, float rc2, uint32_t code,
+                                          float jsz, uint32_t rc2m1, uint32_t code,
                                           uint32_t *__restrict__ lst, int &cnt) {
-  for (int j = j0; j < j1; ++j) {
-    const float4 pj = __ldg(pos + j);
-    float dx, dy, dz;
+  int j = j0;
+  for (; j + 1 < j1; j += 2) {
+    const float4 p0 = __ldg(pos + j);
+    const float4 p1 = __ldg(pos + j + 1);
+    float dx0, dy0, dz0, dx1, dy1, dz1;
     if constexpr (JSHIFT) {
-      dx = ax - (pj.x - jsx);
-      dy = ay - (pj.y - jsy);
-      dz = az - (pj.z - jsz);
+      dx0 = ax - (p0.x - jsx);
+      dy0 = ay - (p0.y - jsy);
+      dz0 = az - (p0.z - jsz);
+      dx1 = ax - (p1.x - jsx);
+      dy1 = ay - (p1.y - jsy);
+      dz1 = az - (p1.z - jsz);
     } else {
-      dx = ax - pj.x;
-      dy = ay - pj.y;
-      dz = az - pj.z;
+      dx0 = ax - p0.x;
+      dy0 = ay - p0.y;
+      dz0 = az - p0.z;
+      dx1 = ax - p1.x;
+      dy1 = ay - p1.y;
+      dz1 = az - p1.z;
     }
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool hit = (r2 < rc2) & (r2 > 0.0f);
+    const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
+    const float r21 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
     lst[cnt * NT] = (uint32_t)j | code;
-    cnt += hit ? 1 : 0;
-    if (cnt == CAP) return j;
+    cnt += in_range(r20, rc2m1) ? 1 : 0;
+    lst[cnt * NT] = (uint32_t)(j + 1) | code;
+    cnt += in_range(r21, rc2m1) ? 1 : 0;
+    if (cnt > CAP - 2) return j + 2;
+  }
+  if (j < j1) {
+    const float4 p0 = __ldg(pos + j);
+    float dx0, dy0, dz0;
+    if constexpr (JSHIFT) {
+      dx0 = ax - (p0.x - jsx);
+      dy0 = ay - (p0.y - jsy);
+      dz0 = az - (p0.z - jsz);
+    } else {
+      dx0 = ax - p0.x;
+      dy0 = ay - p0.y;
+      dz0 = az - p0.z;
+    }
+    const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
+    lst[cnt * NT] = (uint32_t)j | code;
+    cnt += in_range(r20, rc2m1) ? 1 : 0;
+    if (cnt > CAP - 2) return j + 1;
   }
   return -1;
 }
 
 // Force on one target particle in slot p from the 27-cell (full) or 13-cell
 // + own-cell (half) neighbourhood, reading neighbours from global memory.
-// Every lane of the warp must call this (dead lanes with alive = false) since
-// list drains are decided warp-wide.
+// Every lane of the warp must call this (dead lanes with alive = false):
+// the rows are walked in a warp-uniform loop and the lists are drained at a
+// single warp-uniform point, when a list is nearly full or after a row once
+// any lane holds more than CAP/2 entries.
 template <bool HALF, int NT, int CAP>
 __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,
                                              int p, bool alive, uint32_t *__restrict__ lst) {
-  constexpr int FLUSH = CAP / 2;  // a warp drains its lists after a row once any lane exceeds this
+  static_assert(CAP >= 4, "list too short");
+  constexpr int FLUSH = CAP / 2;
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
   if (alive) {
     pi = P.pos[p];
@@ -80,6 +118,8 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   const uint32_t slo = (uint32_t)S.step, shi = (uint32_t)(S.step >> 32);
   const float Lx = B.L[0], Ly = B.L[1], Lz = B.L[2];
   const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const uint32_t rc2m1 = __float_as_uint(B.rc2) - 1u;
+  const bool k_is_one = (B.kexp == 1.0f);
 
   float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
   int cnt = 0;
@@ -105,7 +145,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       const float rinv = rsqrtf(r2);
       const float r = r2 * rinv;
       const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
-      const float wR = (B.kexp == 1.0f) ? w : powf(w, B.kexp);
+      const float wR = k_is_one ? w : powf(w, B.kexp);
       const float ev = fmaf(dx, vi.x - vj.x, fmaf(dy, vi.y - vj.y, dz * (vi.z - vj.z))) * rinv;
       const uint32_t u = pair_word(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
       const float fc = B.a * w;
@@ -123,48 +163,20 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     cnt = 0;
   };
 
-  // One contiguous slot range with a fixed image code; drains when the list fills.
-  auto range = [&](int j0, int j1, float ax, float ay, float az, float jsx, float jsy, float jsz,
-                   uint32_t code) {
-    while (j0 < j1) {
-      const int stop = (code & (kCodeJX | kCodeJY | kCodeJZ))
-                           ? scan_range<true, NT, CAP>(P.pos, j0, j1, ax, ay, az, jsx, jsy, jsz,
-                                                       B.rc2, code, lst, cnt)
-                           : scan_range<false, NT, CAP>(P.pos, j0, j1, ax, ay, az, 0.f, 0.f, 0.f,
-                                                        B.rc2, code, lst, cnt);
-      if (stop < 0) break;
-      drain();
-      j0 = stop + 1;
-    }
-  };
-
-  // Cells cx-1..cx+1 (or cx..cx+1 from `xlo`) of one row; one range unless
-  // the row crosses an x face.
-  auto row = [&](int rowbase, float ay, float az, float jsy, float jsz, uint32_t code) {
-    if (cx >= 1 && cx <= nx - 2) {
-      range(__ldg(P.start + rowbase + cx - 1), __ldg(P.start + rowbase + cx + 2), pi.x, ay, az,
-            0.f, jsy, jsz, code);
+  // Rows of the stencil.  Full: (dy, dz) in {-1,0,1}^2.  Half: the own row
+  // (own cell after p, then cell cx+1), row dy=+1 of the own plane, and the
+  // three rows of the plane dz=+1.
+  constexpr int NROWS = HALF ? 5 : 9;
+#pragma unroll 1
+  for (int r = 0; r < NROWS; ++r) {
+    int dy, dz;
+    if constexpr (HALF) {
+      dz = (r < 2) ? 0 : 1;
+      dy = (r == 0) ? 0 : (r == 1 ? 1 : r - 3);
     } else {
-      for (int dxc = -1; dxc <= 1; ++dxc) {
-        int x = cx + dxc;
-        float ax = pi.x, jsx = 0.f;
-        uint32_t c = code;
-        if (x < 0) {
-          x += nx;
-          jsx = Lx;
-          c |= kCodeJX;
-        } else if (x >= nx) {
-          x -= nx;
-          ax = pi.x - Lx;
-          c |= kCodeIX;
-        }
-        range(__ldg(P.start + rowbase + x), __ldg(P.start + rowbase + x + 1), ax, ay, az, jsx,
-              jsy, jsz, c);
-      }
+      dz = r / 3 - 1;
+      dy = r - 3 * (r / 3) - 1;
     }
-  };
-
-  auto rowfor = [&](int dy, int dz) {
     int z = cz + dz, y = cy + dy;
     float az = pi.z, jsz = 0.f, ay = pi.y, jsy = 0.f;
     uint32_t code = 0;
@@ -186,31 +198,70 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       ay = pi.y - Ly;
       code |= kCodeIY;
     }
-    if (alive) row(B.cellBase + (z * ny + y) * nx, ay, az, jsy, jsz, code);
-    if (__any_sync(0xffffffffu, cnt > FLUSH)) drain();
-  };
-
-  if constexpr (!HALF) {
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy) rowfor(dy, dz);
-  } else {
-    // Half stencil: own cell (slots after p) and cell cx+1 of the own row, the
-    // row dy=+1 of the own plane, and the three rows of the plane dz=+1.
-    if (alive) {
-      const int rowbase = B.cellBase + (cz * ny + cy) * nx;
-      if (cx + 1 <= nx - 1) {
-        range(p + 1, __ldg(P.start + rowbase + cx + 2), pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, 0u);
+    const int rowbase = B.cellBase + (z * ny + y) * nx;
+    // Segments of this row: one contiguous slot range, or (across an x
+    // face) one range per cell with its own image shift.
+    const bool own = HALF && r == 0;
+    const bool inner = own ? (cx + 1 <= nx - 1) : (cx >= 1 && cx <= nx - 2);
+    const int nseg = alive ? (inner ? 1 : (own ? 2 : 3)) : 0;
+    auto segment = [&](int sg, int &j0, int &j1, float &ax, float &jsx, uint32_t &c) {
+      ax = pi.x;
+      jsx = 0.f;
+      c = code;
+      if (inner) {
+        j0 = own ? p + 1 : __ldg(P.start + rowbase + cx - 1);
+        j1 = __ldg(P.start + rowbase + cx + 2);
+      } else if (own) {  // cx == nx - 1: own cell after p, then cell 0 seen from r_i - L
+        if (sg == 0) {
+          j0 = p + 1;
+          j1 = __ldg(P.start + rowbase + cx + 1);
+        } else {
+          j0 = __ldg(P.start + rowbase);
+          j1 = __ldg(P.start + rowbase + 1);
+          ax = pi.x - Lx;
+          c |= kCodeIX;
+        }
       } else {
-        range(p + 1, __ldg(P.start + rowbase + cx + 1), pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, 0u);
-        range(__ldg(P.start + rowbase), __ldg(P.start + rowbase + 1), pi.x - Lx, pi.y, pi.z, 0.f,
-              0.f, 0.f, kCodeIX);
+        int x = cx + sg - 1;
+        if (x < 0) {
+          x += nx;
+          jsx = Lx;
+          c |= kCodeJX;
+        } else if (x >= nx) {
+          x -= nx;
+          ax = pi.x - Lx;
+          c |= kCodeIX;
+        }
+        j0 = __ldg(P.start + rowbase + x);
+        j1 = __ldg(P.start + rowbase + x + 1);
       }
+    };
+    int sg = 0, j = 0, j1 = 0;
+    float ax = 0.f, jsx = 0.f;
+    uint32_t c = 0;
+    if (nseg > 0) segment(0, j, j1, ax, jsx, c);
+    for (;;) {
+      bool more = false;
+      if (sg < nseg) {
+        const int stop = (c & (kCodeJX | kCodeJY | kCodeJZ))
+                             ? scan_range<true, NT, CAP>(P.pos, j, j1, ax, ay, az, jsx, jsy, jsz,
+                                                         rc2m1, c, lst, cnt)
+                             : scan_range<false, NT, CAP>(P.pos, j, j1, ax, ay, az, 0.f, 0.f, 0.f,
+                                                          rc2m1, c, lst, cnt);
+        if (stop >= 0 && stop < j1) {
+          j = stop;  // list nearly full: continue this segment after a drain
+          more = true;
+        } else if (++sg < nseg) {
+          segment(sg, j, j1, ax, jsx, c);
+          more = true;
+        }
+      }
+      const bool any_more = __any_sync(0xffffffffu, more);
+      if (__any_sync(0xffffffffu, cnt > CAP - 2) ||
+          (!any_more && __any_sync(0xffffffffu, cnt > FLUSH)))
+        drain();
+      if (!any_more) break;
     }
-    if (__any_sync(0xffffffffu, cnt > FLUSH)) drain();
-    rowfor(1, 0);
-    rowfor(-1, 1);
-    rowfor(0, 1);
-    rowfor(1, 1);
   }
   drain();
 
