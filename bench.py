@@ -322,6 +322,8 @@ def run_native(args):
     n = x.shape[0]
     stream = torch.cuda.current_stream()
     tiling = dict(tiles=args.tiles, tile_cells=args.tile_cells, stage_cap=args.stage_cap)
+    if args.variant is not None:
+        tiling["variant"] = args.variant
     box = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed + rank,
                   stencil=(1 if args.stencil == "half" else 0), stream=stream, **tiling)
     box.set_state(x, v)
@@ -372,6 +374,19 @@ def run_native(args):
             gbs = STAGE_BYTES[name] * n / (t / 1000.0) / 1e9
             d.update({"GB/s": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3)})
         stages[name] = d
+
+    # ---- the other stencil on the same state, for the half-vs-full comparison
+    other = "full" if args.stencil == "half" else "half"
+    obox = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed + rank,
+                   stencil=(1 if other == "half" else 0), stream=stream)
+    obox.set_state(x, v)
+    obox.step(args.warmup)
+    ostage = obox.profile(min(args.steps, 50))
+    obox.close()
+    stencils = {args.stencil: {"force_ms": round(stage_ms[4], 5), "step_ms": round(sum(stage_ms), 5),
+                               "deterministic": args.stencil == "full"},
+                other: {"force_ms": round(ostage[4], 5), "step_ms": round(sum(ostage), 5),
+                        "deterministic": other == "full"}}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -435,6 +450,7 @@ def run_native(args):
                          "peak_from": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_mhz} MHz "
                                       f"({clock_src})"},
             "stages": stages,
+            "stencils": stencils,
             "gpu_launches": dpd.KERNELS_PER_STEP * args.steps,
             "clocks": clk,
             "e2e": e2e,
@@ -459,9 +475,10 @@ def main():
     ap.add_argument("--L", type=float, default=128.0)
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--stencil", choices=("full", "half"), default="full")
+    ap.add_argument("--stencil", choices=("full", "half"), default="half")
     ap.add_argument("--tiles", type=int, default=None, help="1: staged force tiles, 0: direct")
     ap.add_argument("--tile-cells", type=int, default=None)
+    ap.add_argument("--variant", type=int, default=None, help="force-kernel variant (default: tuned)")
     ap.add_argument("--stage-cap", type=int, default=None)
     ap.add_argument("--cpu-L", type=float, default=64.0)
     ap.add_argument("--cpu-steps", type=int, default=10)

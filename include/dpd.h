@@ -187,7 +187,7 @@ DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uin
  * batches pick their variants from it when their state is laid out, or
  * after dpd_tuning_apply.  The package's autotuner measures the variants
  * per band on the GPU and sets the table. */
-#define DPD_NUM_FORCE_VARIANTS 7
+#define DPD_NUM_FORCE_VARIANTS 10
 #define DPD_MAX_DENSITY_BANDS 8
 /* threads per block and list capacity of variant v; DPD_ERR_ARG if out of range */
 DPD_API int dpd_force_variant_info(int v, int *threads, int *list_capacity);

@@ -43,7 +43,7 @@ __device__ __forceinline__ bool in_range(float r2, uint32_t rc2_bits_minus_1) {
 // loaded per iteration.  Needs at least 2 free list entries on entry.
 // Returns the next slot to scan when the list has fewer than 2 free entries,
 // or -1 when the range was scanned completely.
-template <bool JSHIFT, int NT, int CAP>
+template <bool JSHIFT, int LS, int CAP>
 __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0, int j1,
                                           float ax, float ay, float az, float jsx, float jsy,
                                           float jsz, uint32_t rc2m1, uint32_t code,
@@ -70,9 +70,9 @@ __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0
     }
     const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
     const float r21 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
-    lst[cnt * NT] = (uint32_t)j | code;
+    lst[cnt * LS] = (uint32_t)j | code;
     cnt += in_range(r20, rc2m1) ? 1 : 0;
-    lst[cnt * NT] = (uint32_t)(j + 1) | code;
+    lst[cnt * LS] = (uint32_t)(j + 1) | code;
     cnt += in_range(r21, rc2m1) ? 1 : 0;
     if (cnt > CAP - 2) return j + 2;
   }
@@ -89,7 +89,7 @@ __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0
       dz0 = az - p0.z;
     }
     const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
-    lst[cnt * NT] = (uint32_t)j | code;
+    lst[cnt * LS] = (uint32_t)j | code;
     cnt += in_range(r20, rc2m1) ? 1 : 0;
     if (cnt > CAP - 2) return j + 1;
   }
@@ -102,11 +102,23 @@ __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0
 // the rows are walked in a warp-uniform loop and the lists are drained at a
 // single warp-uniform point, when a list is nearly full or after a row once
 // any lane holds more than CAP/2 entries.
-template <bool HALF, int NT, int CAP>
+// Per-warp scratch of the balanced drain.  List of lane l: list[l * (CAP+1) + k].
+template <int CAP>
+struct WarpScratch {
+  uint32_t list[32 * (CAP + 1)];
+  float4 own_pos[32];   // each lane's target position (w: id bits)
+  float4 own_vel[32];
+  float4 res[32];       // pair results of the chunk being processed
+  int start[32];        // lane whose list starts at this chunk position, or -1
+};
+
+template <bool HALF, int NT, int CAP, bool BAL = false>
 __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,
-                                             int p, bool alive, uint32_t *__restrict__ lst) {
+                                             int p, bool alive, uint32_t *__restrict__ lst,
+                                             WarpScratch<CAP> *W = nullptr) {
   static_assert(CAP >= 4, "list too short");
   constexpr int FLUSH = CAP / 2;
+  constexpr int LS = BAL ? 1 : NT;  // list stride: own row of the warp scratch, or a column
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
   if (alive) {
     pi = P.pos[p];
@@ -124,41 +136,97 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
   int cnt = 0;
 
+  // Pair force of one list entry for a target at (qi, ui): F_ij (3) and r . F^C.
+  auto pair = [&](uint32_t e, const float4 &qi, const float4 &ui) -> float4 {
+    const int j = (int)(e & kSlotMask);
+    const float4 pj = __ldg(P.pos + j);
+    const float4 vj = __ldg(P.vel + j);
+    float dx, dy, dz;
+    if (e & ~kSlotMask) {  // pair across a box face (rare)
+      dx = ((e & kCodeIX) ? qi.x - Lx : qi.x) - ((e & kCodeJX) ? pj.x - Lx : pj.x);
+      dy = ((e & kCodeIY) ? qi.y - Ly : qi.y) - ((e & kCodeJY) ? pj.y - Ly : pj.y);
+      dz = ((e & kCodeIZ) ? qi.z - Lz : qi.z) - ((e & kCodeJZ) ? pj.z - Lz : pj.z);
+    } else {
+      dx = qi.x - pj.x;
+      dy = qi.y - pj.y;
+      dz = qi.z - pj.z;
+    }
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
+    const float wR = k_is_one ? w : powf(w, B.kexp);
+    const float ev = fmaf(dx, ui.x - vj.x, fmaf(dy, ui.y - vj.y, dz * (ui.z - vj.z))) * rinv;
+    const uint32_t u = pair_word(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
+                                 B.seed_lo, B.seed_hi);
+    const float fc = B.a * w;
+    const float s = fmaf(B.sig * wR, noise_int(u), fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
+    // rounded products (no fusion into the caller's sums), so that every
+    // drain order-preserving variant adds exactly the same terms
+    const float4 g = make_float4(__fmul_rn(s, dx), __fmul_rn(s, dy), __fmul_rn(s, dz),
+                                 __fmul_rn(fc, r));
+    if constexpr (HALF) atomicAdd(P.frc + j, make_float4(-g.x, -g.y, -g.z, g.w));
+    return g;
+  };
+
+  // Balanced drain: the warp's list entries are processed 32 at a time, one
+  // per lane whatever lane owns them; each owner then adds its results in
+  // list order, so every particle's sum has the same order as in the per-lane
+  // drain.
+  auto drain_balanced = [&]() {
+    const int lane = threadIdx.x & 31;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int off = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    W->own_pos[lane] = make_float4(pi.x, pi.y, pi.z, __uint_as_float(idi));
+    W->own_vel[lane] = vi;
+    int carry = 0;
+    for (int base = 0; base < total; base += 32) {
+      W->start[lane] = -1;
+      __syncwarp();
+      if (cnt > 0 && off >= base && off < base + 32) W->start[off - base] = lane;
+      __syncwarp();
+      const unsigned starts = __ballot_sync(0xffffffffu, W->start[lane] >= 0);
+      const unsigned upto = starts & (0xffffffffu >> (31 - lane));
+      const int owner = upto ? W->start[31 - __clz(upto)] : carry;
+      const int offo = __shfl_sync(0xffffffffu, off, owner);
+      const int g = base + lane;
+      float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g < total)
+        res = pair(W->list[owner * (CAP + 1) + (g - offo)], W->own_pos[owner], W->own_vel[owner]);
+      W->res[lane] = res;
+      __syncwarp();
+      const int lo = max(off - base, 0), hi = min(off + cnt - base, 32);
+      for (int q = lo; q < hi; ++q) {
+        const float4 t = W->res[q];
+        fx += t.x;
+        fy += t.y;
+        fz += t.z;
+        vir += t.w;
+      }
+      carry = __shfl_sync(0xffffffffu, owner, 31);
+      __syncwarp();
+    }
+    cnt = 0;
+  };
+
   auto drain = [&]() {
+    if constexpr (BAL) {
+      drain_balanced();
+      return;
+    }
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = lst[k * NT];
-      const int j = (int)(e & kSlotMask);
-      const float4 pj = __ldg(P.pos + j);
-      const float4 vj = __ldg(P.vel + j);
-      float dx, dy, dz;
-      if (e & ~kSlotMask) {  // pair across a box face (rare)
-        dx = ((e & kCodeIX) ? pi.x - Lx : pi.x) - ((e & kCodeJX) ? pj.x - Lx : pj.x);
-        dy = ((e & kCodeIY) ? pi.y - Ly : pi.y) - ((e & kCodeJY) ? pj.y - Ly : pj.y);
-        dz = ((e & kCodeIZ) ? pi.z - Lz : pi.z) - ((e & kCodeJZ) ? pj.z - Lz : pj.z);
-      } else {
-        dx = pi.x - pj.x;
-        dy = pi.y - pj.y;
-        dz = pi.z - pj.z;
-      }
-      const uint32_t idj = __float_as_uint(pj.w);
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float rinv = rsqrtf(r2);
-      const float r = r2 * rinv;
-      const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
-      const float wR = k_is_one ? w : powf(w, B.kexp);
-      const float ev = fmaf(dx, vi.x - vj.x, fmaf(dy, vi.y - vj.y, dz * (vi.z - vj.z))) * rinv;
-      const uint32_t u = pair_word(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
-      const float fc = B.a * w;
-      const float s = fmaf(B.sig * wR, noise_int(u), fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
-      const float gx = s * dx, gy = s * dy, gz = s * dz;
-      fx += gx;
-      fy += gy;
-      fz += gz;
-      const float vterm = fc * r;
-      vir += vterm;
-      if constexpr (HALF) {
-        atomicAdd(P.frc + j, make_float4(-gx, -gy, -gz, vterm));
-      }
+      const float4 g = pair(lst[k * LS], pi, vi);
+      fx += g.x;
+      fy += g.y;
+      fz += g.z;
+      vir += g.w;
     }
     cnt = 0;
   };
@@ -244,9 +312,9 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       bool more = false;
       if (sg < nseg) {
         const int stop = (c & (kCodeJX | kCodeJY | kCodeJZ))
-                             ? scan_range<true, NT, CAP>(P.pos, j, j1, ax, ay, az, jsx, jsy, jsz,
+                             ? scan_range<true, LS, CAP>(P.pos, j, j1, ax, ay, az, jsx, jsy, jsz,
                                                          rc2m1, c, lst, cnt)
-                             : scan_range<false, NT, CAP>(P.pos, j, j1, ax, ay, az, 0.f, 0.f, 0.f,
+                             : scan_range<false, LS, CAP>(P.pos, j, j1, ax, ay, az, 0.f, 0.f, 0.f,
                                                           rc2m1, c, lst, cnt);
         if (stop >= 0 && stop < j1) {
           j = stop;  // list nearly full: continue this segment after a drain
@@ -287,16 +355,24 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
 }
 
 // One thread per target slot in [slot0, slot1).
-template <bool SINGLE, bool HALF, int NT, int CAP>
+template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL>
 __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
-  __shared__ uint32_t smem_list[CAP * NT];
+  constexpr int kListWords = BAL ? 1 : CAP * NT;
+  __shared__ uint32_t smem_list[kListWords];
+  __shared__ WarpScratch<BAL ? CAP : 4> smem_warp[BAL ? NT / 32 : 1];
   const int p = slot0 + blockIdx.x * NT + threadIdx.x;
   bool alive = p < slot1;
   const int b = (!SINGLE && alive) ? find_box(P.pbase, P.nbox, p) : 0;
   const BoxDev B = box_of<SINGLE>(P, b);
   const BoxState S = P.st[b];
   alive = alive && S.adv;
-  force_direct<HALF, NT, CAP>(P, B, S, p, alive, smem_list + threadIdx.x);
+  if constexpr (BAL) {
+    WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
+    force_direct<HALF, NT, CAP, true>(P, B, S, p, alive, W->list + (threadIdx.x & 31) * (CAP + 1),
+                                      W);
+  } else {
+    force_direct<HALF, NT, CAP, false>(P, B, S, p, alive, smem_list + threadIdx.x);
+  }
 }
 
 // ------------------------------------------------------- staged force tiles
@@ -584,8 +660,10 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
 struct VariantInfo {
   int threads, cap;
 };
+// Variants 7..9 use the balanced drain.
 static const VariantInfo kVariants[kNumForceVariants] = {
-    {128, 24}, {128, 16}, {128, 32}, {256, 24}, {64, 24}, {64, 32}, {256, 32}};
+    {128, 24}, {128, 16}, {128, 32}, {256, 24}, {64, 24}, {64, 32}, {256, 32},
+    {64, 24}, {128, 24}, {256, 24}};
 
 int force_variant_info(int v, int *threads, int *cap) {
   if (v < 0 || v >= kNumForceVariants) return -1;
@@ -594,9 +672,10 @@ int force_variant_info(int v, int *threads, int *cap) {
   return 0;
 }
 
-template <bool SINGLE, bool HALF, int NT, int CAP>
+template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL = false>
 static void launch_k(const Packed &P, int s0, int s1, cudaStream_t s) {
-  if (s1 > s0) k_force<SINGLE, HALF, NT, CAP><<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
+  if (s1 > s0)
+    k_force<SINGLE, HALF, NT, CAP, BAL><<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
 }
 
 template <bool SINGLE, bool HALF>
@@ -608,6 +687,9 @@ static void launch_variant(int v, const Packed &P, int s0, int s1, cudaStream_t 
     case 4: launch_k<SINGLE, HALF, 64, 24>(P, s0, s1, s); break;
     case 5: launch_k<SINGLE, HALF, 64, 32>(P, s0, s1, s); break;
     case 6: launch_k<SINGLE, HALF, 256, 32>(P, s0, s1, s); break;
+    case 7: launch_k<SINGLE, HALF, 64, 24, true>(P, s0, s1, s); break;
+    case 8: launch_k<SINGLE, HALF, 128, 24, true>(P, s0, s1, s); break;
+    case 9: launch_k<SINGLE, HALF, 256, 24, true>(P, s0, s1, s); break;
     default: launch_k<SINGLE, HALF, 128, 24>(P, s0, s1, s); break;
   }
 }

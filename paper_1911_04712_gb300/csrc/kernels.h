@@ -45,7 +45,7 @@ struct ForceBand {
   int slot0, slot1, variant;
 };
 constexpr int kMaxBands = 8;
-constexpr int kNumForceVariants = 7;
+constexpr int kNumForceVariants = 10;
 
 // How a step is launched.
 struct StepConfig {

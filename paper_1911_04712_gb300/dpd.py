@@ -147,7 +147,7 @@ class Box:
     def __init__(self, L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, *,
                  stencil=None, kexp=None, mass=None, body_force=None, poiseuille_f=None,
                  flow_axis=None, grad_axis=None, stream=None, tiles=None, tile_cells=None,
-                 stage_cap=None):
+                 stage_cap=None, variant=None):
         L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
         self.L = tuple(float(v) for v in L3)
         self._ctx = ctypes.c_void_p()
@@ -158,7 +158,7 @@ class Box:
                          (PARAM_KEXP, kexp), (PARAM_MASS, mass), (PARAM_BODYFORCE, body_force),
                          (PARAM_POISEUILLE_F, poiseuille_f), (PARAM_STENCIL, stencil),
                          (PARAM_FORCE_TILES, tiles), (PARAM_TILE_CELLS, tile_cells),
-                         (PARAM_STAGE_CAP, stage_cap)):
+                         (PARAM_STAGE_CAP, stage_cap), (PARAM_FORCE_VARIANT, variant)):
             if val is not None:
                 self.set_param(key, val)
         if stream is not None:
