@@ -76,14 +76,14 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
       k0 += kPhiloxW0;
       k1 += kPhiloxW1;
     }
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;  // one wide multiply each
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
     c0 = n0;
-    c1 = lo1;
+    c1 = (uint32_t)p1;
     c2 = n2;
-    c3 = lo0;
+    c3 = (uint32_t)p0;
   }
   return c0;
 }
@@ -140,6 +140,18 @@ __device__ __forceinline__ int find_box(const int *__restrict__ pbase, int nbox,
       hi = mid - 1;
   }
   return lo;
+}
+
+// find_box for a warp of consecutive slots: one search for the warp's first
+// slot, a per-lane search only for lanes past that box's end.  All lanes of
+// the warp must call it.
+__device__ __forceinline__ int find_box_warp(const int *__restrict__ pbase, int nbox, int p) {
+  const int p0 = __shfl_sync(0xffffffffu, p, 0);
+  int b0 = 0;
+  if ((threadIdx.x & 31) == 0) b0 = find_box(pbase, nbox, p0);
+  b0 = __shfl_sync(0xffffffffu, b0, 0);
+  const int end0 = __ldg(pbase + b0 + 1);
+  return (p >= p0 && p < end0) ? b0 : find_box(pbase, nbox, p);
 }
 
 }  // namespace dpd

@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   __shared__ WarpScratch<BAL ? CAP : 4> smem_warp[BAL ? NT / 32 : 1];
   const int p = slot0 + blockIdx.x * NT + threadIdx.x;
   bool alive = p < slot1;
-  const int b = (!SINGLE && alive) ? find_box(P.pbase, P.nbox, p) : 0;
+  int b = 0;
+  if constexpr (!SINGLE) b = find_box_warp(P.pbase, P.nbox, min(p, P.ntot - 1));
   const BoxDev B = box_of<SINGLE>(P, b);
   const BoxState S = P.st[b];
   alive = alive && S.adv;

@@ -63,8 +63,9 @@ __device__ __forceinline__ float refold(float x, float L) {
 template <bool SINGLE>
 __global__ void __launch_bounds__(kBinThreads) k_integrate_bin(Packed P, bool move) {
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
+  int b = 0;
+  if constexpr (!SINGLE) b = find_box_warp(P.pbase, P.nbox, min(p, P.ntot - 1));
   if (p >= P.ntot) return;
-  const int b = SINGLE ? 0 : find_box(P.pbase, P.nbox, p);
   const BoxDev B = box_of<SINGLE>(P, b);
   float4 x = P.pos[p];
   float4 v = P.vel[p];
