@@ -62,6 +62,22 @@ STAGE_BYTES = {
 }
 
 
+# DRAM traffic of the force kernel per launch from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/force_direct_L128_rho3.md),
+# valid only while the kernel sources hash to the value recorded with it.
+TRAFFIC = {("half", 128.0, 3.0): (391.249e6, "71252e49a99b4757")}
+KERNEL_SOURCES = ("paper_1911_04712_gb300/csrc/force.cu",)
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
 
@@ -364,6 +380,10 @@ def run_native(args):
         clock_src = "median SM clock under load from MEASURED_PEAKS.json"
     alu_peak = sms * 128 * float(sm_mhz) * 1e6 / 1e12 if sm_mhz else None   # T lane-ops/s
     force_ms = stage_ms[4]
+    traffic = None
+    rec = TRAFFIC.get((args.stencil, float(L), float(rho)))
+    if rec and rec[1] == kernel_hash():
+        traffic = rec[0]
     slots = force_slots_per_particle(rho) * n
     achieved = slots / (force_ms / 1000.0) / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -446,7 +466,8 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "kernel": "force", "achieved": achieved,
                          "peak": alu_peak, "unit": "T lane-ops/s",
-                         "frac": (achieved / alu_peak) if alu_peak else None, "traffic": None,
+                         "frac": (achieved / alu_peak) if alu_peak else None,
+                         "traffic": traffic,
                          "peak_from": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_mhz} MHz "
                                       f"({clock_src})"},
             "stages": stages,
