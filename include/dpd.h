@@ -158,6 +158,18 @@ typedef struct {
 
 DPD_API int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out);
 
+/* ---------------------------------------------------------- checkpoints */
+/* A checkpoint holds the context's internal state as the device keeps it:
+ * positions, velocities (v(n - 1/2) after the first step), forces, in the
+ * current cell order, with the step counter.  Loading it into a context
+ * created with the same box and parameters continues the run exactly
+ * (bitwise with the full stencil).  `buf` is host memory of
+ * dpd_checkpoint_size() bytes; loading checks its header.
+ * Errors: DPD_ERR_STATE (nothing loaded / mismatched header), DPD_ERR_ARG. */
+DPD_API int64_t dpd_checkpoint_size(const dpd_ctx *ctx);
+DPD_API int dpd_checkpoint_save(dpd_ctx *ctx, void *buf, int64_t bytes);
+DPD_API int dpd_checkpoint_load(dpd_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Number of particles loaded (0 before dpd_set_state). */
 DPD_API int64_t dpd_num_particles(const dpd_ctx *ctx);
 

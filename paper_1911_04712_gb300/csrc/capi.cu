@@ -1,6 +1,7 @@
 // C ABI of the single-box context (dpd_*) and the debug entry points.
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <new>
 
 #include "dpd.h"
@@ -223,6 +224,83 @@ int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out) {
   out->step = (int64_t)ctx->eng.box_state(0).step;
   out->n = n;
   return ctx->eng.check_error();
+}
+
+namespace {
+struct CheckpointHeader {
+  char magic[8];       // "DPDCKPT1"
+  int64_t n;
+  double box[3], a, gamma, kT, rc, dt;
+  uint64_t seed;
+  unsigned long long step;
+  long long remaining;
+  int pending, stencil;
+};
+}  // namespace
+
+int64_t dpd_checkpoint_size(const dpd_ctx *ctx) {
+  if (!ctx) return 0;
+  return (int64_t)sizeof(CheckpointHeader) + ctx->n * 3 * (int64_t)sizeof(float4);
+}
+
+int dpd_checkpoint_save(dpd_ctx *ctx, void *buf, int64_t bytes) {
+  dpd::clear_error();
+  if (!ctx || !buf) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  if (!ctx->loaded) return dpd::set_error(DPD_ERR_STATE, "no state loaded");
+  if (bytes < dpd_checkpoint_size(ctx))
+    return dpd::set_error(DPD_ERR_ARG, "buffer of %lld bytes, need %lld", (long long)bytes,
+                          (long long)dpd_checkpoint_size(ctx));
+  CheckpointHeader h{};
+  std::memcpy(h.magic, "DPDCKPT1", 8);
+  h.n = ctx->n;
+  for (int k = 0; k < 3; ++k) h.box[k] = ctx->bp.L[k];
+  h.a = ctx->bp.a;
+  h.gamma = ctx->bp.gamma;
+  h.kT = ctx->bp.kT;
+  h.rc = ctx->bp.rc;
+  h.dt = ctx->bp.dt;
+  h.seed = ctx->bp.seed;
+  const dpd::BoxState &st = ctx->eng.box_state(0);
+  h.step = st.step;
+  h.remaining = st.remaining;
+  h.pending = st.pending;
+  h.stencil = ctx->eng.step_config().stencil;
+  std::memcpy(buf, &h, sizeof h);
+  float4 *arr = reinterpret_cast<float4 *>(static_cast<char *>(buf) + sizeof h);
+  return ctx->eng.copy_box_raw(0, arr, arr + ctx->n, arr + 2 * ctx->n, true);
+}
+
+int dpd_checkpoint_load(dpd_ctx *ctx, const void *buf, int64_t bytes) {
+  dpd::clear_error();
+  if (!ctx || !buf) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  if (bytes < (int64_t)sizeof(CheckpointHeader))
+    return dpd::set_error(DPD_ERR_ARG, "buffer too small for a checkpoint");
+  CheckpointHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, "DPDCKPT1", 8) != 0)
+    return dpd::set_error(DPD_ERR_STATE, "not a checkpoint");
+  const dpd::BoxParams &bp = ctx->bp;
+  if (h.box[0] != bp.L[0] || h.box[1] != bp.L[1] || h.box[2] != bp.L[2] || h.a != bp.a ||
+      h.gamma != bp.gamma || h.kT != bp.kT || h.rc != bp.rc || h.dt != bp.dt || h.seed != bp.seed)
+    return dpd::set_error(DPD_ERR_STATE, "checkpoint was made with other box parameters");
+  if (h.n < 0 || bytes < (int64_t)sizeof h + h.n * 3 * (int64_t)sizeof(float4))
+    return dpd::set_error(DPD_ERR_ARG, "checkpoint buffer truncated");
+  ctx->loaded = false;
+  int rc = ctx->eng.layout({ctx->bp}, {h.n});
+  if (rc) return rc;
+  const float4 *arr = reinterpret_cast<const float4 *>(static_cast<const char *>(buf) + sizeof h);
+  rc = ctx->eng.copy_box_raw(0, const_cast<float4 *>(arr), const_cast<float4 *>(arr + h.n),
+                             const_cast<float4 *>(arr + 2 * h.n), false);
+  if (rc) return rc;
+  dpd::BoxState st{h.step, h.remaining, h.pending, 1};
+  ctx->eng.set_box_state_raw(0, st);
+  rc = ctx->eng.set_stencil(h.stencil);
+  if (rc) return rc;
+  rc = ctx->eng.rebuild();  // cell list from the saved order; force recomputed at the saved step
+  if (rc) return rc;
+  ctx->n = h.n;
+  ctx->loaded = true;
+  return DPD_OK;
 }
 
 int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms) {

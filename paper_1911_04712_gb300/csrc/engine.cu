@@ -642,6 +642,23 @@ int Engine::build_work() {
   return DPD_OK;
 }
 
+int Engine::copy_box_raw(int box, float4 *pos, float4 *vel, float4 *frc, bool to_host) {
+  if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
+  const size_t n = (size_t)(pbase_[box + 1] - pbase_[box]), o = (size_t)pbase_[box];
+  const cudaMemcpyKind k = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+  float4 *dev[3] = {d_.pos + o, d_.vel + o, d_.frc + o};
+  float4 *host[3] = {pos, vel, frc};
+  for (int a = 0; a < 3; ++a) {
+    if (!host[a] || n == 0) continue;
+    if (to_host)
+      DPD_CUDA_TRY(cudaMemcpyAsync(host[a], dev[a], n * sizeof(float4), k, stream_));
+    else
+      DPD_CUDA_TRY(cudaMemcpyAsync(dev[a], host[a], n * sizeof(float4), k, stream_));
+  }
+  DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  return DPD_OK;
+}
+
 int Engine::box_sums(std::vector<double> &sums) {
   const int nb = nbox();
   if (work_dirty_) {

@@ -103,6 +103,10 @@ class Engine {
   int check_error();                // reads and clears the device error word
 
   int gather(int box, float *pos, float *vel, float *frc, bool device_ptr);
+  // Raw slot-order copies of one box's pos / vel / frc (float4) to or from
+  // host memory, for checkpoints.  Synchronises the stream.
+  int copy_box_raw(int box, float4 *pos, float4 *vel, float4 *frc, bool to_host);
+  void set_box_state_raw(int box, const BoxState &s) { st_host_[box] = s; }
 
   // ---- served form
   // Statistics sampling every `every` box steps into per-box FP64

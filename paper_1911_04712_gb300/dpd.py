@@ -79,6 +79,12 @@ def lib():
     L.dpd_num_particles.restype = i64
     L.dpd_profile_steps.argtypes = [vp, i64, c.POINTER(dbl)]
     L.dpd_profile_steps.restype = i32
+    L.dpd_checkpoint_size.argtypes = [vp]
+    L.dpd_checkpoint_size.restype = i64
+    L.dpd_checkpoint_save.argtypes = [vp, vp, i64]
+    L.dpd_checkpoint_save.restype = i32
+    L.dpd_checkpoint_load.argtypes = [vp, vp, i64]
+    L.dpd_checkpoint_load.restype = i32
     L.dpd_debug_rng.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp]
     L.dpd_forces_noalloc.argtypes = [i64, vp, vp, c.POINTER(dbl), dbl, dbl, dbl, dbl, dbl, u64,
                                      u64, vp, vp]
@@ -250,6 +256,22 @@ class Box:
         ms = (ctypes.c_double * NUM_STAGES)()
         check(lib().dpd_profile_steps(self._ctx, int(nsteps), ms))
         return list(ms)
+
+    def checkpoint(self) -> bytes:
+        """Internal state (cell order, step counter) as bytes."""
+        n = lib().dpd_checkpoint_size(self._ctx)
+        buf = ctypes.create_string_buffer(n)
+        check(lib().dpd_checkpoint_save(self._ctx, buf, n))
+        return buf.raw
+
+    def restore(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        check(lib().dpd_checkpoint_load(self._ctx, buf, len(data)))
+        self.n = self._n_from_header(data)
+
+    @staticmethod
+    def _n_from_header(data: bytes) -> int:
+        return int(np.frombuffer(data[8:16], dtype=np.int64)[0])
 
     def stats(self) -> dict:
         s = Stats()

@@ -341,3 +341,30 @@ def test_tiling_knobs_reported(dpd):
     assert box.tiling() == {"tiles": 1, "tile_cells": 5, "stage_cap": 512}
     with pytest.raises(dpd.DPDError):
         box.set_param(dpd.PARAM_STAGE_CAP, 10)
+
+
+# ------------------------------------------------------------ checkpoints
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_checkpoint_resume(dpd, stencil):
+    L = 7.0
+    x, v = uniform_box_state(L, rho=3, seed=12)
+    p = _params(L, seed=12)
+    a = _box(dpd, p, stencil)
+    a.set_state(x, v)
+    a.step(50)
+    ck = a.checkpoint()
+    a.step(50)
+    xa, va = a.get_state()
+    b = _box(dpd, p, stencil)
+    b.restore(ck)
+    assert b.stats()["step"] == 50
+    b.step(50)
+    xb, vb = b.get_state()
+    if stencil == 0:
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    else:
+        assert np.abs(_min_image(xa.astype(np.float64) - xb, L)).max() < 1e-4
+    other = _box(dpd, _params(L, seed=13), stencil)
+    with pytest.raises(dpd.DPDError) as ei:
+        other.restore(ck)
+    assert ei.value.code == dpd.ERR_STATE

@@ -90,3 +90,18 @@ def test_budget_and_cancel(S):
     with pytest.raises(D.DPDError):
         q.result(12345)
     q.close()
+
+
+def test_bounded_wait_reports_timeout(S):
+    """A chunk wait limit shorter than the chunk: the queue reports
+    DPD_ERR_TIMEOUT for its runs (the GPU work itself completes normally)."""
+    D = pytest.importorskip("paper_1911_04712_gb300.dpd")
+    q = S.Queue(1 << 30, chunk_steps=100, chunk_timeout_s=1e-7)
+    t = q.submit(S.make_request(32.0, rho=3, seed=1, steps=400))
+    with pytest.raises(D.DPDError) as ei:
+        q.wait_all(120)
+    assert ei.value.code == D.ERR_TIMEOUT
+    assert q.result(t)["status"] == D.ERR_TIMEOUT
+    with pytest.raises(D.DPDError):
+        q.submit(S.make_request(8.0, rho=3, steps=10))
+    q.close()
