@@ -95,6 +95,12 @@ typedef struct dpd_ctx dpd_ctx;
 #define DPD_PARAM_FORCE_VARIANT 11 /* direct force-kernel variant 0..DPD_NUM_FORCE_VARIANTS-1, or -1
                                       (default) to pick per density band from the tuning table */
 
+#define DPD_PARAM_NOISE 12        /* DPD_NOISE_UNIFORM (default) or DPD_NOISE_GAUSSIAN */
+
+#define DPD_NOISE_UNIFORM 0   /* xi = sqrt(3)(2U - 1): uniform, unit variance, bit-exact on CPU */
+#define DPD_NOISE_GAUSSIAN 1  /* xi Gaussian as Sec. 2.1 states: Box-Muller on words 0 and 1,
+                                 sqrt(-2 ln U1) cos(2 pi U2); within rounding of libm */
+
 #define DPD_STENCIL_FULL 0  /* 27 cells, each thread sums its own pairs: no atomics,
                                bitwise reproducible */
 #define DPD_STENCIL_HALF 1  /* 13 cells + own cell, Newton's third law with atomics
@@ -184,12 +190,13 @@ DPD_API int64_t dpd_num_particles(const dpd_ctx *ctx);
 DPD_API int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms);
 
 /* ---------------------------------------------------------------- debug */
-/* Raw noise words for n pairs (lo[k], hi[k]) at a step and seed: word 0 of
- * Philox-4x32-10 on (min, max, step lo, step hi) keyed by (seed lo, seed hi).
- * lo, hi, out are DEVICE pointers; xi (may be NULL) receives the FP32 noise
- * values.  Runs on the given stream (NULL = default) and synchronises it. */
+/* Raw noise words for n pairs (lo[k], hi[k]) at a step and seed: words 0
+ * and 1 of Philox-4x32-10 on (min, max, step lo, step hi) keyed by (seed lo,
+ * seed hi).  lo, hi, out0 are DEVICE pointers; out1 and xi may be NULL; xi
+ * receives the FP32 noise of the given DPD_NOISE_* mode.  Runs on the given
+ * stream (NULL = default) and synchronises it. */
 DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uint64_t step, uint64_t seed,
-                  uint32_t *out, float *xi, void *stream);
+                  int noise, uint32_t *out0, uint32_t *out1, float *xi, void *stream);
 
 /* --------------------------------------------------------- kernel tuning */
 /* The direct force kernel comes in variants that differ in threads per
@@ -230,7 +237,7 @@ typedef struct {
     int body_mode;       /* 0 none, 1 constant, 2 periodic Poiseuille (Sec. 4.2) */
     int flow_axis;       /* axis of the body force */
     int grad_axis;       /* axis on which the Poiseuille force switches sign */
-    int pad_;
+    int noise;           /* DPD_NOISE_UNIFORM or DPD_NOISE_GAUSSIAN */
 } dpd_box_desc;
 
 /* Create a batch of nbox boxes and allocate its device memory.
@@ -291,7 +298,7 @@ typedef struct {
     double body_force;       /* 0: none */
     int body_mode;           /* 1 constant, 2 periodic Poiseuille (Sec. 4.2) */
     int flow_axis, grad_axis;
-    int pad_;
+    int noise;               /* DPD_NOISE_UNIFORM or DPD_NOISE_GAUSSIAN */
 } dpd_request;
 
 typedef struct {

@@ -50,6 +50,7 @@ class _Params(ctypes.Structure):
         ("fb_grad", ctypes.c_int),
         ("rounds", ctypes.c_int),
         ("seed", ctypes.c_uint64),
+        ("noise", ctypes.c_int),
     ]
 
 
@@ -70,12 +71,13 @@ class Params:
     fb_grad: int = 0
     rounds: int = 10
     seed: int = 0
+    noise: int = 0   # 0 uniform, 1 Gaussian
 
     def c(self) -> _Params:
         L = np.broadcast_to(np.asarray(self.L, dtype=np.float64), (3,))
         return _Params((ctypes.c_double * 3)(*L), self.a, self.gamma, self.kT, self.rc,
                        self.dt, self.mass, self.kexp, self.fb, self.fb_mode, self.fb_flow,
-                       self.fb_grad, self.rounds, self.seed)
+                       self.fb_grad, self.rounds, self.seed, self.noise)
 
 
 def build(force: bool = False) -> str:
@@ -109,6 +111,10 @@ def _load():
     lib.orc_xi_from_word.restype = ctypes.c_double
     lib.orc_rng.argtypes = [ctypes.c_int64, u32p, u32p, ctypes.c_uint64, ctypes.c_uint64,
                             ctypes.c_int, u32p, dp]
+    lib.orc_rng_gauss.argtypes = [ctypes.c_int64, u32p, u32p, ctypes.c_uint64, ctypes.c_uint64,
+                                  ctypes.c_int, u32p, u32p, dp]
+    lib.orc_xi_gauss.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+    lib.orc_xi_gauss.restype = ctypes.c_double
     lib.orc_pair_force.argtypes = [pp, dp, dp, dp, dp, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint64, dp, dp]
     lib.orc_forces.argtypes = [pp, ctypes.c_int64, dp, dp, u32p, ctypes.c_uint64, ctypes.c_int,
@@ -169,6 +175,25 @@ def pair_rng(ida, idb, step: int, seed: int, rounds: int = 10):
     lib.orc_rng(n, _ptr(a, ctypes.c_uint32), _ptr(b, ctypes.c_uint32), step, seed, rounds,
                 _ptr(words, ctypes.c_uint32), _ptr(xi, ctypes.c_double))
     return words, xi
+
+
+def pair_rng_gauss(ida, idb, step: int, seed: int, rounds: int = 10):
+    """Words 0, 1 and the Gaussian noise values for the pairs (ida[k], idb[k])."""
+    lib = _load()
+    a = np.ascontiguousarray(ida, dtype=np.uint32)
+    b = np.ascontiguousarray(idb, dtype=np.uint32)
+    n = a.size
+    w0 = np.zeros(n, dtype=np.uint32)
+    w1 = np.zeros(n, dtype=np.uint32)
+    xi = np.zeros(n, dtype=np.float64)
+    lib.orc_rng_gauss(n, _ptr(a, ctypes.c_uint32), _ptr(b, ctypes.c_uint32), step, seed, rounds,
+                      _ptr(w0, ctypes.c_uint32), _ptr(w1, ctypes.c_uint32),
+                      _ptr(xi, ctypes.c_double))
+    return w0, w1, xi
+
+
+def xi_gauss(u0: int, u1: int) -> float:
+    return _load().orc_xi_gauss(int(u0), int(u1))
 
 
 def xi_from_word(u: int) -> float:

@@ -11,7 +11,8 @@
  *     unit variance), drawn from the Philox-4x32-R counter-based generator of
  *     Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as
  *     1, 2, 3" (SC'11), with counter (min id, max id, step lo, step hi) and
- *     key (seed lo, seed hi); xi = sqrt(3) (2U - 1), U = ((u >> 8) + 1/2) 2^-24;
+ *     key (seed lo, seed hi); xi = sqrt(3) (2U - 1), U = ((u >> 8) + 1/2) 2^-24,
+ *     or, as the paper states it, Gaussian: Box-Muller on words 0 and 1;
  *   - the pair force of Sec. 2.1: Eq. 3 (conservative), Eq. 4 (weight w),
  *     Eq. 5 (dissipative and random), the fluctuation-dissipation relation
  *     sigma^2 = 2 gamma kT, w_D = w_R^2, and the generalised weight
@@ -54,6 +55,7 @@ typedef struct {
     int fb_grad;     /* axis along which the Poiseuille force switches sign */
     int rounds;      /* Philox rounds R */
     uint64_t seed;
+    int noise;       /* 0: uniform xi = sqrt(3)(2U - 1); 1: Gaussian xi (Box-Muller) */
 } orc_params;
 
 /* ----------------------------------------------------------------------
@@ -108,6 +110,44 @@ double orc_xi_from_word(uint32_t u)
     return sqrt(3.0) * (2.0 * U - 1.0);
 }
 
+/* Words 0 and 1 of the pair's Philox block (same counter and key). */
+void orc_pair_words(uint32_t id_i, uint32_t id_j, uint64_t step, uint64_t seed, int rounds,
+                    uint32_t out[2])
+{
+    uint32_t ctr[4], key[2], w[4];
+    ctr[0] = id_i < id_j ? id_i : id_j;
+    ctr[1] = id_i < id_j ? id_j : id_i;
+    ctr[2] = (uint32_t)(step & 0xffffffffu);
+    ctr[3] = (uint32_t)(step >> 32);
+    key[0] = (uint32_t)(seed & 0xffffffffu);
+    key[1] = (uint32_t)(seed >> 32);
+    orc_philox4x32(ctr, key, rounds, w);
+    out[0] = w[0];
+    out[1] = w[1];
+}
+
+/* The paper's Gaussian xi (Sec. 2.1) by the Box-Muller transform of two
+ * uniforms U_k = ((u_k >> 8) + 1/2) 2^-24: sqrt(-2 ln U1) cos(2 pi U2). */
+double orc_xi_gauss(uint32_t u0, uint32_t u1)
+{
+    const double pi = 3.14159265358979323846;
+    double U1 = ((double)(u0 >> 8) + 0.5) * (1.0 / 16777216.0);
+    double U2 = ((double)(u1 >> 8) + 0.5) * (1.0 / 16777216.0);
+    return sqrt(-2.0 * log(U1)) * cos(2.0 * pi * U2);
+}
+
+void orc_rng_gauss(int64_t n, const uint32_t *ida, const uint32_t *idb, uint64_t step,
+                   uint64_t seed, int rounds, uint32_t *w0, uint32_t *w1, double *xi)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        uint32_t u[2];
+        orc_pair_words(ida[k], idb[k], step, seed, rounds, u);
+        if (w0) w0[k] = u[0];
+        if (w1) w1[k] = u[1];
+        if (xi) xi[k] = orc_xi_gauss(u[0], u[1]);
+    }
+}
+
 void orc_rng(int64_t n, const uint32_t *ida, const uint32_t *idb, uint64_t step, uint64_t seed,
              int rounds, uint32_t *words, double *xi)
 {
@@ -155,7 +195,14 @@ void orc_pair_force(const orc_params *p, const double *xi, const double *xj,
     double wD = wR * wR;                              /* w_D = w_R^2 */
     double sigma = sqrt(2.0 * p->gamma * p->kT);      /* sigma^2 = 2 gamma kT */
     double ev = e[0] * (vi[0] - vj[0]) + e[1] * (vi[1] - vj[1]) + e[2] * (vi[2] - vj[2]);
-    double xi_ij = orc_xi_from_word(orc_pair_word(idi, idj, step, p->seed, p->rounds));
+    double xi_ij;
+    if (p->noise == 1) {
+        uint32_t u[2];
+        orc_pair_words(idi, idj, step, p->seed, p->rounds, u);
+        xi_ij = orc_xi_gauss(u[0], u[1]);
+    } else {
+        xi_ij = orc_xi_from_word(orc_pair_word(idi, idj, step, p->seed, p->rounds));
+    }
     double FC = p->a * w;                             /* Eq. 3 */
     double FD = -p->gamma * ev * wD;                  /* Eq. 5, dissipative */
     double FR = sigma * xi_ij * wR / sqrt(p->dt);     /* Eq. 5, random */

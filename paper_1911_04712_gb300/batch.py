@@ -21,7 +21,7 @@ class BoxDesc(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("n", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("kexp", ctypes.c_double), ("mass", ctypes.c_double),
                 ("body_force", ctypes.c_double), ("body_mode", ctypes.c_int),
-                ("flow_axis", ctypes.c_int), ("grad_axis", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("flow_axis", ctypes.c_int), ("grad_axis", ctypes.c_int), ("noise", ctypes.c_int)]
 
 
 def declare(L):
@@ -99,10 +99,11 @@ def tuning_get(stencil: int):
 
 
 def make_desc(L, n, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, steps=0, kexp=1.0,
-              mass=1.0, body_force=0.0, body_mode=0, flow_axis=2, grad_axis=0) -> BoxDesc:
+              mass=1.0, body_force=0.0, body_mode=0, flow_axis=2, grad_axis=0,
+              noise=0) -> BoxDesc:
     L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
     return BoxDesc((ctypes.c_double * 3)(*L3), a, gamma, kT, rc, dt, int(seed), int(n),
-                   int(steps), kexp, mass, body_force, body_mode, flow_axis, grad_axis, 0)
+                   int(steps), kexp, mass, body_force, body_mode, flow_axis, grad_axis, noise)
 
 
 class Batch:

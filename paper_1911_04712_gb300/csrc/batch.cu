@@ -101,6 +101,7 @@ int dpd_batch_create(dpd_batch **out, int nbox, const dpd_box_desc *descs) {
     bp.fb_flow = d.flow_axis;
     bp.fb_grad = d.grad_axis;
     bp.seed = d.seed;
+    bp.noise = d.noise;
     int nc[3];
     int rc = dpd::check_params(bp, nc);
     if (rc) return dpd::set_error(rc, "box %d: %s", i, dpd_last_error());

@@ -111,6 +111,11 @@ int dpd_set_param(dpd_ctx *ctx, int key, double value) {
       ctx->stage_cap = cap;
       return DPD_OK;
     }
+    case DPD_PARAM_NOISE:
+      if (!(value == DPD_NOISE_UNIFORM || value == DPD_NOISE_GAUSSIAN))
+        return dpd::set_error(DPD_ERR_ARG, "noise must be DPD_NOISE_UNIFORM or DPD_NOISE_GAUSSIAN");
+      bp.noise = (int)value;
+      break;
     case DPD_PARAM_FORCE_VARIANT:
       if (!(value >= -1.0 && value < DPD_NUM_FORCE_VARIANTS) || value != std::floor(value))
         return dpd::set_error(DPD_ERR_ARG, "force variant must be -1..%d",
@@ -143,6 +148,7 @@ int dpd_get_param(const dpd_ctx *ctx, int key, double *value) {
     case DPD_PARAM_FORCE_TILES: *value = cfg.tiles ? 1.0 : 0.0; break;
     case DPD_PARAM_TILE_CELLS: *value = ctx->loaded ? cfg.grid.tc : ctx->tile_cells; break;
     case DPD_PARAM_STAGE_CAP: *value = ctx->loaded ? cfg.grid.stage_cap : ctx->stage_cap; break;
+    case DPD_PARAM_NOISE: *value = bp.noise; break;
     case DPD_PARAM_FORCE_VARIANT:
       *value = (ctx->loaded && cfg.nbands > 0) ? cfg.band[0].variant : ctx->eng.variant_override();
       break;
@@ -314,13 +320,15 @@ int dpd_profile_steps(dpd_ctx *ctx, int64_t nsteps, double *stage_ms) {
 int64_t dpd_num_particles(const dpd_ctx *ctx) { return ctx ? ctx->n : 0; }
 
 int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uint64_t step, uint64_t seed,
-                  uint32_t *out, float *xi, void *stream) {
+                  int noise, uint32_t *out0, uint32_t *out1, float *xi, void *stream) {
   dpd::clear_error();
   if (n < 0) return dpd::set_error(DPD_ERR_ARG, "negative count");
+  if (noise != DPD_NOISE_UNIFORM && noise != DPD_NOISE_GAUSSIAN)
+    return dpd::set_error(DPD_ERR_ARG, "bad noise mode");
   if (n == 0) return DPD_OK;
-  if (!lo || !hi || !out) return dpd::set_error(DPD_ERR_ARG, "null device pointer");
+  if (!lo || !hi || !out0) return dpd::set_error(DPD_ERR_ARG, "null device pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  DPD_CUDA_TRY(dpd::launch_debug_rng(lo, hi, n, step, seed, out, xi, s));
+  DPD_CUDA_TRY(dpd::launch_debug_rng(lo, hi, n, step, seed, noise, out0, out1, xi, s));
   DPD_CUDA_TRY(cudaStreamSynchronize(s));
   return DPD_OK;
 }

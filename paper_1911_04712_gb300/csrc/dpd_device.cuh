@@ -55,7 +55,8 @@ struct BoxDev {
   float fb_half;    // L[fb_grad] / 2
   uint32_t seed_lo; // noise key
   uint32_t seed_hi;
-  int pad_;
+  int noise;        // 0: uniform xi of unit variance, 1: Gaussian xi (Box-Muller)
+  float sig_g;      // sigma / sqrt(dt): multiplies a Gaussian xi
 };
 
 // Mutable per-box step state (device resident so that graphs can replay it).
@@ -88,6 +89,28 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
   return c0;
 }
 
+// Words 0 and 1 of Philox-4x32-R (word 1 is the low half of the last
+// round's second product).
+__device__ __forceinline__ uint2 philox_word01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < DPD_PHILOX_ROUNDS; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c0 = n0;
+    c1 = (uint32_t)p1;
+    c2 = n2;
+    c3 = (uint32_t)p0;
+  }
+  return make_uint2(c0, c1);
+}
+
 // Signed odd integer t = 2 (u >> 8) + 1 - 2^24, exactly representable in FP32;
 // xi = sqrt(3) (2U - 1) = sqrt(3) t 2^-24 with U = ((u >> 8) + 1/2) 2^-24.
 __device__ __forceinline__ float noise_int(uint32_t u) {
@@ -100,6 +123,20 @@ __device__ __forceinline__ uint32_t pair_word(uint32_t ida, uint32_t idb, uint32
                                               uint32_t seed_hi) {
   const uint32_t lo = min(ida, idb), hi = max(ida, idb);
   return philox_word0(lo, hi, step_lo, step_hi, seed_lo, seed_hi);
+}
+
+__device__ __forceinline__ uint2 pair_words(uint32_t ida, uint32_t idb, uint32_t step_lo,
+                                            uint32_t step_hi, uint32_t seed_lo, uint32_t seed_hi) {
+  const uint32_t lo = min(ida, idb), hi = max(ida, idb);
+  return philox_word01(lo, hi, step_lo, step_hi, seed_lo, seed_hi);
+}
+
+// Gaussian xi from two words by the Box-Muller transform:
+// sqrt(-2 ln U1) cos(2 pi U2), U_k = ((u_k >> 8) + 1/2) 2^-24.
+__device__ __forceinline__ float gauss_xi(uint32_t u0, uint32_t u1) {
+  const float U1 = fmaf((float)(u0 >> 8), 5.9604645e-08f, 2.9802322e-08f);
+  const float U2 = fmaf((float)(u1 >> 8), 5.9604645e-08f, 2.9802322e-08f);
+  return sqrtf(-2.0f * logf(U1)) * cospif(2.0f * U2);
 }
 
 // ---------------------------------------------------------------- geometry

@@ -53,6 +53,7 @@ int check_params(const BoxParams &bp, int n[3]) {
     return set_error(DPD_ERR_ARG, "bad body force");
   if (bp.fb_flow < 0 || bp.fb_flow > 2 || bp.fb_grad < 0 || bp.fb_grad > 2)
     return set_error(DPD_ERR_ARG, "body-force axes must be 0, 1 or 2");
+  if (bp.noise != 0 && bp.noise != 1) return set_error(DPD_ERR_ARG, "noise must be 0 or 1");
   return DPD_OK;
 }
 
@@ -72,6 +73,8 @@ BoxDev make_box_dev(const BoxParams &bp, int cellBase, int pbase, int np) {
   d.gamma = (float)bp.gamma;
   const double sigma = std::sqrt(2.0 * bp.gamma * bp.kT);  // fluctuation-dissipation
   d.sig = (float)(sigma * std::sqrt(3.0) / 16777216.0 / std::sqrt(bp.dt));
+  d.sig_g = (float)(sigma / std::sqrt(bp.dt));
+  d.noise = bp.noise;
   d.rc2 = (float)(bp.rc * bp.rc);
   d.inv_rc = (float)(1.0 / bp.rc);
   d.kexp = (float)bp.kexp;

@@ -35,6 +35,7 @@ struct BoxParams {
   int fb_mode;      // 0 none, 1 constant, 2 periodic Poiseuille
   int fb_flow, fb_grad;
   uint64_t seed;
+  int noise;        // 0 uniform, 1 Gaussian
 };
 
 // Validates the parameters and derives the cell grid; returns DPD_OK or DPD_ERR_ARG.

@@ -157,10 +157,18 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
     const float wR = k_is_one ? w : powf(w, B.kexp);
     const float ev = fmaf(dx, ui.x - vj.x, fmaf(dy, ui.y - vj.y, dz * (ui.z - vj.z))) * rinv;
-    const uint32_t u = pair_word(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
+    float fr;  // random term sigma w_R xi / sqrt(dt)
+    if (B.noise == 0) {
+      const uint32_t u = pair_word(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
+                                   B.seed_lo, B.seed_hi);
+      fr = B.sig * wR * noise_int(u);
+    } else {
+      const uint2 u = pair_words(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
                                  B.seed_lo, B.seed_hi);
+      fr = B.sig_g * wR * gauss_xi(u.x, u.y);
+    }
     const float fc = B.a * w;
-    const float s = fmaf(B.sig * wR, noise_int(u), fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
+    const float s = (fr + fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
     // rounded products (no fusion into the caller's sums), so that every
     // drain order-preserving variant adds exactly the same terms
     const float4 g = make_float4(__fmul_rn(s, dx), __fmul_rn(s, dy), __fmul_rn(s, dz),
@@ -598,9 +606,16 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
         const float wR = (B.kexp == 1.0f) ? w : powf(w, B.kexp);
         const float ev =
             fmaf(dx, vi.x - vj.x, fmaf(dy, vi.y - vj.y, dz * (vi.z - vj.z))) * rinv;
-        const uint32_t u = pair_word(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
+        float fr;
+        if (B.noise == 0) {
+          const uint32_t u = pair_word(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
+          fr = B.sig * wR * noise_int(u);
+        } else {
+          const uint2 u = pair_words(idi, idj, slo, shi, B.seed_lo, B.seed_hi);
+          fr = B.sig_g * wR * gauss_xi(u.x, u.y);
+        }
         const float fc = B.a * w;
-        const float sc = fmaf(B.sig * wR, noise_int(u), fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
+        const float sc = (fr + fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
         fx = fmaf(sc, dx, fx);
         fy = fmaf(sc, dy, fy);
         fz = fmaf(sc, dz, fz);

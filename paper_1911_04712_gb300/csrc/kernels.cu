@@ -321,12 +321,14 @@ __global__ void k_gather(Packed P, int box, int slot0, int n, float *__restrict_
 // -------------------------------------------------------------- debug rng
 __global__ void k_debug_rng(const uint32_t *__restrict__ lo, const uint32_t *__restrict__ hi,
                             long long n, uint32_t slo, uint32_t shi, uint32_t klo, uint32_t khi,
-                            uint32_t *__restrict__ out, float *__restrict__ xi) {
+                            int noise, uint32_t *__restrict__ out, uint32_t *__restrict__ out1,
+                            float *__restrict__ xi) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const uint32_t u = pair_word(lo[k], hi[k], slo, shi, klo, khi);
-  out[k] = u;
-  if (xi) xi[k] = __fmul_rn(noise_int(u), kSqrt3Scale);
+  const uint2 u = pair_words(lo[k], hi[k], slo, shi, klo, khi);
+  out[k] = u.x;
+  if (out1) out1[k] = u.y;
+  if (xi) xi[k] = noise ? gauss_xi(u.x, u.y) : __fmul_rn(noise_int(u.x), kSqrt3Scale);
 }
 
 // ------------------------------------------------------ served-form kernels
@@ -589,11 +591,12 @@ cudaError_t launch_gather(const Packed &P, int box, int slot0, int n, float *pos
 }
 
 cudaError_t launch_debug_rng(const uint32_t *lo, const uint32_t *hi, long long n, uint64_t step,
-                             uint64_t seed, uint32_t *out, float *xi, cudaStream_t s) {
+                             uint64_t seed, int noise, uint32_t *out, uint32_t *out1, float *xi,
+                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_debug_rng<<<blocks_for(n, 256), 256, 0, s>>>(lo, hi, n, (uint32_t)step,
                                                  (uint32_t)(step >> 32), (uint32_t)seed,
-                                                 (uint32_t)(seed >> 32), out, xi);
+                                                 (uint32_t)(seed >> 32), noise, out, out1, xi);
   return cudaGetLastError();
 }
 

@@ -133,6 +133,7 @@ cudaError_t launch_sample(const Packed &P, const StatsWork *work, int nwork, con
                           cudaStream_t s);
 
 cudaError_t launch_debug_rng(const uint32_t *lo, const uint32_t *hi, long long n, uint64_t step,
-                             uint64_t seed, uint32_t *out, float *xi, cudaStream_t s);
+                             uint64_t seed, int noise, uint32_t *out, uint32_t *out1, float *xi,
+                             cudaStream_t s);
 
 }  // namespace dpd

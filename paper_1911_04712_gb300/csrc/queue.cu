@@ -325,6 +325,7 @@ int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket) {
   bp.fb_flow = req->flow_axis;
   bp.fb_grad = req->grad_axis;
   bp.seed = req->seed;
+  bp.noise = req->noise;
   int nc[3];
   int rc = dpd::check_params(bp, nc);
   if (rc) return rc;

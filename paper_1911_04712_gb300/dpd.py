@@ -23,6 +23,8 @@ WHERE_HOST, WHERE_DEVICE = 0, 1
 PARAM_KEXP, PARAM_MASS, PARAM_BODYFORCE, PARAM_POISEUILLE_F = 1, 2, 3, 4
 PARAM_FLOW_AXIS, PARAM_GRAD_AXIS, PARAM_STENCIL = 5, 6, 7
 PARAM_FORCE_TILES, PARAM_TILE_CELLS, PARAM_STAGE_CAP, PARAM_FORCE_VARIANT = 8, 9, 10, 11
+PARAM_NOISE = 12
+NOISE_UNIFORM, NOISE_GAUSSIAN = 0, 1
 STENCIL_FULL, STENCIL_HALF = 0, 1
 NUM_STAGES, KERNELS_PER_STEP = 5, 7
 STAGE_NAMES = ("integrate_bin", "scan", "bin_keys", "bin_scatter", "force")
@@ -85,7 +87,7 @@ def lib():
     L.dpd_checkpoint_save.restype = i32
     L.dpd_checkpoint_load.argtypes = [vp, vp, i64]
     L.dpd_checkpoint_load.restype = i32
-    L.dpd_debug_rng.argtypes = [vp, vp, i64, u64, u64, vp, vp, vp]
+    L.dpd_debug_rng.argtypes = [vp, vp, i64, u64, u64, i32, vp, vp, vp, vp]
     L.dpd_forces_noalloc.argtypes = [i64, vp, vp, c.POINTER(dbl), dbl, dbl, dbl, dbl, dbl, u64,
                                      u64, vp, vp]
     L.dpd_forces_noalloc.restype = i32
@@ -153,7 +155,7 @@ class Box:
     def __init__(self, L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, *,
                  stencil=None, kexp=None, mass=None, body_force=None, poiseuille_f=None,
                  flow_axis=None, grad_axis=None, stream=None, tiles=None, tile_cells=None,
-                 stage_cap=None, variant=None):
+                 stage_cap=None, variant=None, noise=None):
         L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
         self.L = tuple(float(v) for v in L3)
         self._ctx = ctypes.c_void_p()
@@ -164,7 +166,8 @@ class Box:
                          (PARAM_KEXP, kexp), (PARAM_MASS, mass), (PARAM_BODYFORCE, body_force),
                          (PARAM_POISEUILLE_F, poiseuille_f), (PARAM_STENCIL, stencil),
                          (PARAM_FORCE_TILES, tiles), (PARAM_TILE_CELLS, tile_cells),
-                         (PARAM_STAGE_CAP, stage_cap), (PARAM_FORCE_VARIANT, variant)):
+                         (PARAM_STAGE_CAP, stage_cap), (PARAM_FORCE_VARIANT, variant),
+                         (PARAM_NOISE, noise)):
             if val is not None:
                 self.set_param(key, val)
         if stream is not None:
@@ -279,8 +282,10 @@ class Box:
         return s.as_dict()
 
 
-def debug_rng(lo, hi, step: int, seed: int, stream=None):
-    """Noise words (uint32) and FP32 xi for pairs (lo[k], hi[k]) computed on the GPU."""
+def debug_rng(lo, hi, step: int, seed: int, stream=None, noise: int = NOISE_UNIFORM,
+              word1: bool = False):
+    """Noise words (uint32) and FP32 xi for pairs (lo[k], hi[k]) computed on the GPU;
+    with word1=True also Philox word 1."""
     import torch
     lo = np.ascontiguousarray(lo, dtype=np.uint32)
     hi = np.ascontiguousarray(hi, dtype=np.uint32)
@@ -288,11 +293,16 @@ def debug_rng(lo, hi, step: int, seed: int, stream=None):
     d_lo = torch.from_numpy(lo.view(np.int32)).cuda()
     d_hi = torch.from_numpy(hi.view(np.int32)).cuda()
     d_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    d_out1 = torch.empty(n, dtype=torch.int32, device="cuda")
     d_xi = torch.empty(n, dtype=torch.float32, device="cuda")
     check(lib().dpd_debug_rng(ctypes.c_void_p(d_lo.data_ptr()), ctypes.c_void_p(d_hi.data_ptr()),
-                              n, int(step), int(seed), ctypes.c_void_p(d_out.data_ptr()),
+                              n, int(step), int(seed), int(noise),
+                              ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_out1.data_ptr()),
                               ctypes.c_void_p(d_xi.data_ptr()), _stream_ptr(stream)))
-    return d_out.cpu().numpy().view(np.uint32), d_xi.cpu().numpy()
+    w0 = d_out.cpu().numpy().view(np.uint32)
+    if word1:
+        return w0, d_out1.cpu().numpy().view(np.uint32), d_xi.cpu().numpy()
+    return w0, d_xi.cpu().numpy()
 
 
 NOALLOC_MAX_PARTICLES = 32768

@@ -22,7 +22,7 @@ class Request(ctypes.Structure):
                 ("rc", ctypes.c_double), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("steps", ctypes.c_int64), ("body_force", ctypes.c_double),
                 ("body_mode", ctypes.c_int), ("flow_axis", ctypes.c_int),
-                ("grad_axis", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("grad_axis", ctypes.c_int), ("noise", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -84,10 +84,11 @@ def _check(rc):
 
 
 def make_request(L, rho=0.0, n=0, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0,
-                 steps=1000, body_force=0.0, body_mode=0, flow_axis=2, grad_axis=0) -> Request:
+                 steps=1000, body_force=0.0, body_mode=0, flow_axis=2, grad_axis=0,
+                 noise=0) -> Request:
     L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
     return Request((ctypes.c_double * 3)(*L3), rho, int(n), a, gamma, kT, rc, dt, int(seed),
-                   int(steps), body_force, body_mode, flow_axis, grad_axis, 0)
+                   int(steps), body_force, body_mode, flow_axis, grad_axis, noise)
 
 
 class Queue:

@@ -368,3 +368,32 @@ def test_checkpoint_resume(dpd, stencil):
     with pytest.raises(dpd.DPDError) as ei:
         other.restore(ck)
     assert ei.value.code == dpd.ERR_STATE
+
+
+# ------------------------------------------------ Gaussian noise (Sec. 2.1)
+def test_gaussian_noise_words_and_values(dpd):
+    rng = np.random.default_rng(8)
+    n = 1 << 14
+    lo = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    hi = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    w0, w1, xi = dpd.debug_rng(lo, hi, 123, 456, noise=dpd.NOISE_GAUSSIAN, word1=True)
+    r0, r1, rxi = O.pair_rng_gauss(lo, hi, 123, 456)
+    assert np.array_equal(w0, r0) and np.array_equal(w1, r1)
+    assert np.abs(xi.astype(np.float64) - rxi).max() < 2e-6 * max(1.0, np.abs(rxi).max())
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_gaussian_noise_forces_and_trajectory(dpd, stencil):
+    L = 8.0
+    x, v = uniform_box_state(L, rho=3, seed=2)
+    p = _params(L, seed=2, noise=1)
+    box = _box(dpd, p, stencil)
+    box.set_param(dpd.PARAM_NOISE, dpd.NOISE_GAUSSIAN)
+    box.set_state(x, v)
+    f_ref, _ = O.forces(p, x, v, 0)
+    _force_check(box.get_forces(), f_ref)
+    box.step(100)
+    xg, _ = box.get_state()
+    s = O.State(p, x, v)
+    s.run(100)
+    assert np.abs(_min_image(xg.astype(np.float64) - s.x, L)).max() < TRAJ_TOL

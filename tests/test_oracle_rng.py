@@ -139,3 +139,34 @@ def test_xi_uncorrelated_across_steps_and_pairs():
     tol = 5.0 / math.sqrt(n)
     for other in (x1, x2, x3):
         assert abs(np.mean(x0 * other)) < tol
+
+
+# ------------------------------------------------ Gaussian reading (Sec. 2.1)
+def test_gaussian_xi_words_are_the_block_words_and_symmetric():
+    rng = np.random.default_rng(21)
+    a = rng.integers(0, 2**32, 1000, dtype=np.uint64).astype(np.uint32)
+    b = rng.integers(0, 2**32, 1000, dtype=np.uint64).astype(np.uint32)
+    w0, w1, xi = O.pair_rng_gauss(a, b, 9, 77)
+    w0b, w1b, xib = O.pair_rng_gauss(b, a, 9, 77)
+    assert np.array_equal(w0, w0b) and np.array_equal(w1, w1b) and np.array_equal(xi, xib)
+    for k in range(20):
+        lo, hi = min(a[k], b[k]), max(a[k], b[k])
+        blk = O.philox4x32([lo, hi, 9, 0], [77, 0])
+        assert w0[k] == blk[0] and w1[k] == blk[1]
+    # Box-Muller on its own closed form: U2 = 1/4 + 2^-26 gives cos(pi/2 + ...) ~ 0
+    assert abs(O.xi_gauss(0x80000000, 0x40000000)) < 1e-6
+
+
+def test_gaussian_xi_statistics_normal():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    n = 2_000_000
+    ida = np.arange(n, dtype=np.uint32)
+    _, _, xi = O.pair_rng_gauss(ida, ida + np.uint32(7), 4, 31)
+    m, var = xi.mean(), xi.var()
+    kurt = ((xi - m) ** 4).mean() / var ** 2
+    assert abs(m) < 5 / math.sqrt(n)
+    assert abs(var - 1) < 5 * math.sqrt(2.0 / n)
+    assert abs(kurt - 3.0) < 5 * math.sqrt(24.0 / n)
+    # against the normal CDF of a library (Kolmogorov-Smirnov, 5 sigma-ish level)
+    ks = scipy_stats.kstest(xi[:200000], "norm")
+    assert ks.pvalue > 1e-6

@@ -80,3 +80,18 @@ def test_pressure_approaches_groot_warren_fit():
     # ... and the distance to the 0.101 fit shrinks with density
     assert abs(devs[0]) > abs(devs[1]) > abs(devs[2])
     assert all(abs(d) < 0.10 for d in devs)
+
+
+def test_thermostat_with_gaussian_noise():
+    L, dt, kT = 6, 0.005, 1.0
+    x, v = uniform_box_state(L, rho=3, kT=kT, seed=23)
+    p = O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=kT, dt=dt, seed=19, noise=1)
+    s = O.State(p, x, v, mode=O.MODE_CELLS)
+    s.run(600)
+    samples = []
+    for _ in range(1200):
+        s.run(5)
+        samples.append(s.stats()["kT"])
+    m, err = _block_mean(samples)
+    print(f"Gaussian noise: kT {m:.5f} +- {err:.5f}")
+    assert abs(m - kT) <= 0.01 * kT + 3.0 * err
