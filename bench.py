@@ -220,7 +220,8 @@ def run_batched(args, stream, world, rank):
     n_tot = sum(len(x) for x, _ in states)
     descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
              for s, st in zip(specs, states)]
-    bt = B.Batch(descs, stream=stream)
+    stencil = 1 if args.stencil == "half" else 0
+    bt = B.Batch(descs, stream=stream, stencil=stencil)
     for k, (x, v) in enumerate(states):
         bt.set_state(k, x, v)
     bt.step(args.warmup)
@@ -236,7 +237,8 @@ def run_batched(args, stream, world, rank):
 
     boxes = []
     for s, (x, v) in zip(specs, states):
-        b = dpd.Box(s.L, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed, stream=stream)
+        b = dpd.Box(s.L, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed, stream=stream,
+                    stencil=stencil)
         b.set_state(x, v)
         b.step(args.warmup)
         boxes.append(b)
@@ -260,6 +262,7 @@ def run_batched(args, stream, world, rank):
     return {"workload": f"box mix: {args.nbox} boxes, L~U{{6..24}}, rho in {{3,4,5}}, "
                         f"a~U[10,80], gamma~U[2,8], kT~U[0.5,2], dt=0.005",
             "boxes": args.nbox, "particles": n_tot, "steps": args.batch_steps,
+            "stencil": args.stencil,
             "value": rate_b, "unit": UNIT, "ms_per_step": ms_b / args.batch_steps,
             "one_box_at_a_time": {"value": rate_s, "ms_per_step": ms_s / args.batch_steps},
             "speedup_vs_one_at_a_time": rate_b / rate_s,
@@ -279,7 +282,8 @@ def run_served(args, rank=0, world=1):
 
     reqs = request_stream(args.requests, rate=args.rate, master_seed=args.seed)
     reqs = [reqs[k] for k in shard_requests(len(reqs), rank, world)]
-    q = S.Queue(int(120e9), chunk_steps=100, sample_every=20, nbins=16, policy=S.POLICY_FIFO)
+    q = S.Queue(int(120e9), chunk_steps=100, sample_every=20, nbins=16, policy=S.POLICY_FIFO,
+                stencil=1 if args.stencil == "half" else 0)
     tickets = []
     t0 = time.perf_counter()
     for r in reqs:
@@ -311,6 +315,7 @@ def run_served(args, rank=0, world=1):
             "p50_latency_s": pct(50), "p99_latency_s": pct(99), "max_latency_s": lat[-1],
             "wall_s": wall, "gpu_busy_s": st["busy_seconds"],
             "policy": "first come first served, admission at 100-step chunk boundaries",
+            "stencil": args.stencil,
             "kT_mean_rel_err_median": statistics.median(kt_err)}
 
 

@@ -171,18 +171,23 @@ int Engine::build_bands() {
     const BoxDev &B = boxes_[b];
     const double rho = (double)B.np / ((double)B.L[0] * B.L[1] * B.L[2]);
     const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(cfg_.stencil, rho);
-    if (!runs.empty() && runs.back().variant == v)
+    const int g = B.noise != 0;
+    if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g)
       runs.back().slot1 = pbase_[b + 1];
     else
-      runs.push_back(ForceBand{pbase_[b], pbase_[b + 1], v});
+      runs.push_back(ForceBand{pbase_[b], pbase_[b + 1], v, g});
   }
   if ((int)runs.size() > kMaxBands) {
     // too fragmented (boxes not ordered by band): one launch with the
     // variant that covers the most particles
     std::vector<long long> cover(kNumForceVariants, 0);
-    for (const auto &r : runs) cover[r.variant] += r.slot1 - r.slot0;
+    int anyg = 0;
+    for (const auto &r : runs) {
+      cover[r.variant] += r.slot1 - r.slot0;
+      anyg |= r.gauss;
+    }
     const int best = (int)(std::max_element(cover.begin(), cover.end()) - cover.begin());
-    runs.assign(1, ForceBand{0, ntot_, best});
+    runs.assign(1, ForceBand{0, ntot_, best, anyg});
   }
   cfg_.nbands = (int)runs.size();
   for (int k = 0; k < cfg_.nbands; ++k) cfg_.band[k] = runs[k];

@@ -112,7 +112,7 @@ struct WarpScratch {
   int start[32];        // lane whose list starts at this chunk position, or -1
 };
 
-template <bool HALF, int NT, int CAP, bool BAL = false>
+template <bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false>
 __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,
                                              int p, bool alive, uint32_t *__restrict__ lst,
                                              WarpScratch<CAP> *W = nullptr) {
@@ -158,14 +158,17 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     const float wR = k_is_one ? w : powf(w, B.kexp);
     const float ev = fmaf(dx, ui.x - vj.x, fmaf(dy, ui.y - vj.y, dz * (ui.z - vj.z))) * rinv;
     float fr;  // random term sigma w_R xi / sqrt(dt)
-    if (B.noise == 0) {
+    if constexpr (GAUSS) {  // kernels for bands holding a box with Gaussian noise
+      const uint2 u = pair_words(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
+                                 B.seed_lo, B.seed_hi);
+      if (B.noise == 0)
+        fr = B.sig * wR * noise_int(u.x);
+      else
+        fr = B.sig_g * wR * gauss_xi(u.x, u.y);
+    } else {
       const uint32_t u = pair_word(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
                                    B.seed_lo, B.seed_hi);
       fr = B.sig * wR * noise_int(u);
-    } else {
-      const uint2 u = pair_words(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
-                                 B.seed_lo, B.seed_hi);
-      fr = B.sig_g * wR * gauss_xi(u.x, u.y);
     }
     const float fc = B.a * w;
     const float s = (fr + fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
@@ -279,7 +282,11 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     // face) one range per cell with its own image shift.
     const bool own = HALF && r == 0;
     const bool inner = own ? (cx + 1 <= nx - 1) : (cx >= 1 && cx <= nx - 2);
-    const int nseg = alive ? (inner ? 1 : (own ? 2 : 3)) : 0;
+    // Full stencil: a row across an x face is two ranges (two cells in place,
+    // one image cell).  Half stencil: one range per cell, which keeps its
+    // kernels (with the extra own-row case) below the spill point.
+    constexpr bool kMergeX = !HALF;
+    const int nseg = alive ? (inner ? 1 : ((own || kMergeX) ? 2 : 3)) : 0;
     auto segment = [&](int sg, int &j0, int &j1, float &ax, float &jsx, uint32_t &c) {
       ax = pi.x;
       jsx = 0.f;
@@ -297,7 +304,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
           ax = pi.x - Lx;
           c |= kCodeIX;
         }
-      } else {
+      } else if (!kMergeX) {
         int x = cx + sg - 1;
         if (x < 0) {
           x += nx;
@@ -310,6 +317,26 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
         }
         j0 = __ldg(P.start + rowbase + x);
         j1 = __ldg(P.start + rowbase + x + 1);
+      } else if (cx == 0) {  // cells 0, 1 in place; cell nx-1 as the image r_j - L
+        if (sg == 0) {
+          j0 = __ldg(P.start + rowbase);
+          j1 = __ldg(P.start + rowbase + 2);
+        } else {
+          j0 = __ldg(P.start + rowbase + nx - 1);
+          j1 = __ldg(P.start + rowbase + nx);
+          jsx = Lx;
+          c |= kCodeJX;
+        }
+      } else {  // cx == nx - 1: cells nx-2, nx-1 in place; cell 0 seen from r_i - L
+        if (sg == 0) {
+          j0 = __ldg(P.start + rowbase + nx - 2);
+          j1 = __ldg(P.start + rowbase + nx);
+        } else {
+          j0 = __ldg(P.start + rowbase);
+          j1 = __ldg(P.start + rowbase + 1);
+          ax = pi.x - Lx;
+          c |= kCodeIX;
+        }
       }
     };
     int sg = 0, j = 0, j1 = 0;
@@ -363,7 +390,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
 }
 
 // One thread per target slot in [slot0, slot1).
-template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL>
+template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL, bool GAUSS>
 __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   constexpr int kListWords = BAL ? 1 : CAP * NT;
   __shared__ uint32_t smem_list[kListWords];
@@ -377,10 +404,10 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   alive = alive && S.adv;
   if constexpr (BAL) {
     WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
-    force_direct<HALF, NT, CAP, true>(P, B, S, p, alive, W->list + (threadIdx.x & 31) * (CAP + 1),
-                                      W);
+    force_direct<HALF, NT, CAP, true, GAUSS>(P, B, S, p, alive,
+                                             W->list + (threadIdx.x & 31) * (CAP + 1), W);
   } else {
-    force_direct<HALF, NT, CAP, false>(P, B, S, p, alive, smem_list + threadIdx.x);
+    force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x);
   }
 }
 
@@ -688,14 +715,18 @@ int force_variant_info(int v, int *threads, int *cap) {
   return 0;
 }
 
-template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL = false>
+template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false>
 static void launch_k(const Packed &P, int s0, int s1, cudaStream_t s) {
   if (s1 > s0)
-    k_force<SINGLE, HALF, NT, CAP, BAL><<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
+    k_force<SINGLE, HALF, NT, CAP, BAL, GAUSS><<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
 }
 
 template <bool SINGLE, bool HALF>
-static void launch_variant(int v, const Packed &P, int s0, int s1, cudaStream_t s) {
+static void launch_variant(int v, bool gauss, const Packed &P, int s0, int s1, cudaStream_t s) {
+  if (gauss) {  // one configuration serves bands that hold Gaussian-noise boxes
+    launch_k<SINGLE, HALF, 128, 24, false, true>(P, s0, s1, s);
+    return;
+  }
   switch (v) {
     case 1: launch_k<SINGLE, HALF, 128, 16>(P, s0, s1, s); break;
     case 2: launch_k<SINGLE, HALF, 128, 32>(P, s0, s1, s); break;
@@ -736,21 +767,21 @@ cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s)
       k_force_tiles<false><<<cfg.grid.ntiles, kTileThreads, smem, s>>>(P, cfg.grid);
     return cudaGetLastError();
   }
-  ForceBand whole{0, P.ntot, 0};
+  ForceBand whole{0, P.ntot, 0, 0};
   const ForceBand *bands = cfg.nbands > 0 ? cfg.band : &whole;
   const int nb = cfg.nbands > 0 ? cfg.nbands : 1;
   for (int k = 0; k < nb; ++k) {
     const ForceBand &b = bands[k];
     if (single) {
       if (half)
-        launch_variant<true, true>(b.variant, P, b.slot0, b.slot1, s);
+        launch_variant<true, true>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
       else
-        launch_variant<true, false>(b.variant, P, b.slot0, b.slot1, s);
+        launch_variant<true, false>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
     } else {
       if (half)
-        launch_variant<false, true>(b.variant, P, b.slot0, b.slot1, s);
+        launch_variant<false, true>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
       else
-        launch_variant<false, false>(b.variant, P, b.slot0, b.slot1, s);
+        launch_variant<false, false>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
     }
   }
   return cudaGetLastError();
