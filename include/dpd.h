@@ -200,13 +200,16 @@ DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uin
 
 /* --------------------------------------------------------- kernel tuning */
 /* The direct force kernel comes in variants that differ in threads per
- * block and pair-list entries per thread.  A process-wide table, one per
+ * block, pair-list entries per thread and how a warp drains its lists:
+ * variants 0-6 per lane, 7-9 balanced over the warp in list order, 10-12
+ * spread over the warp with atomic sums (half stencil only; with the full
+ * stencil 10-12 drain per lane).  A process-wide table, one per
  * stencil, maps density bands (upper bounds of rho = N/V, increasing; the
  * last band also takes every higher density) to a variant.  Contexts and
  * batches pick their variants from it when their state is laid out, or
  * after dpd_tuning_apply.  The package's autotuner measures the variants
  * per band on the GPU and sets the table. */
-#define DPD_NUM_FORCE_VARIANTS 10
+#define DPD_NUM_FORCE_VARIANTS 13
 #define DPD_MAX_DENSITY_BANDS 8
 /* threads per block and list capacity of variant v; DPD_ERR_ARG if out of range */
 DPD_API int dpd_force_variant_info(int v, int *threads, int *list_capacity);

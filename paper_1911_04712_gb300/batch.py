@@ -10,7 +10,7 @@ import os
 import numpy as np
 
 BATCH_GRAPH_CHUNK = 100
-NUM_FORCE_VARIANTS = 10
+NUM_FORCE_VARIANTS = 13
 MAX_DENSITY_BANDS = 8
 TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 

@@ -18,6 +18,9 @@ constexpr int kTileListCap = 24;
 
 static inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
+// Candidates loaded per iteration of the candidate pass.
+constexpr int kScanUnroll = 4;
+
 // ------------------------------------------------------------------ force
 // Pair lists: each thread appends the neighbours found inside rc to its own
 // column of a shared-memory list (entry k of thread t at lst[k * NT + t], NT threads),
@@ -39,59 +42,38 @@ __device__ __forceinline__ bool in_range(float r2, uint32_t rc2_bits_minus_1) {
 
 // Candidate pass over slots [j0, j1): appends every j with 0 < r_ij^2 < rc^2.
 // The append is branch-free (the slot is written every candidate and kept
-// only on a hit), so the lanes of a warp stay converged; two candidates are
-// loaded per iteration.  Needs at least 2 free list entries on entry.
-// Returns the next slot to scan when the list has fewer than 2 free entries,
-// or -1 when the range was scanned completely.
-template <bool JSHIFT, int LS, int CAP>
+// only on a hit), so the lanes of a warp stay converged; U candidates are
+// loaded per iteration (the last iteration masked).  Needs at least U free
+// list entries on entry.  Returns the next slot to scan (possibly >= j1) when
+// the list has fewer than U free entries, or -1 when the range was scanned
+// completely.
+template <bool JSHIFT, int LS, int CAP, int U>
 __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0, int j1,
                                           float ax, float ay, float az, float jsx, float jsy,
                                           float jsz, uint32_t rc2m1, uint32_t code,
                                           uint32_t *__restrict__ lst, int &cnt) {
-  int j = j0;
-  for (; j + 1 < j1; j += 2) {
-    const float4 p0 = __ldg(pos + j);
-    const float4 p1 = __ldg(pos + j + 1);
-    float dx0, dy0, dz0, dx1, dy1, dz1;
-    if constexpr (JSHIFT) {
-      dx0 = ax - (p0.x - jsx);
-      dy0 = ay - (p0.y - jsy);
-      dz0 = az - (p0.z - jsz);
-      dx1 = ax - (p1.x - jsx);
-      dy1 = ay - (p1.y - jsy);
-      dz1 = az - (p1.z - jsz);
-    } else {
-      dx0 = ax - p0.x;
-      dy0 = ay - p0.y;
-      dz0 = az - p0.z;
-      dx1 = ax - p1.x;
-      dy1 = ay - p1.y;
-      dz1 = az - p1.z;
+  for (int j = j0; j < j1; j += U) {
+    float4 q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      q[u] = (u == 0 || j + u < j1) ? __ldg(pos + j + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float dx, dy, dz;
+      if constexpr (JSHIFT) {
+        dx = ax - (q[u].x - jsx);
+        dy = ay - (q[u].y - jsy);
+        dz = az - (q[u].z - jsz);
+      } else {
+        dx = ax - q[u].x;
+        dy = ay - q[u].y;
+        dz = az - q[u].z;
+      }
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      lst[cnt * LS] = (uint32_t)(j + u) | code;
+      cnt += ((u == 0 || j + u < j1) && in_range(r2, rc2m1)) ? 1 : 0;
     }
-    const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
-    const float r21 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
-    lst[cnt * LS] = (uint32_t)j | code;
-    cnt += in_range(r20, rc2m1) ? 1 : 0;
-    lst[cnt * LS] = (uint32_t)(j + 1) | code;
-    cnt += in_range(r21, rc2m1) ? 1 : 0;
-    if (cnt > CAP - 2) return j + 2;
-  }
-  if (j < j1) {
-    const float4 p0 = __ldg(pos + j);
-    float dx0, dy0, dz0;
-    if constexpr (JSHIFT) {
-      dx0 = ax - (p0.x - jsx);
-      dy0 = ay - (p0.y - jsy);
-      dz0 = az - (p0.z - jsz);
-    } else {
-      dx0 = ax - p0.x;
-      dy0 = ay - p0.y;
-      dz0 = az - p0.z;
-    }
-    const float r20 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
-    lst[cnt * LS] = (uint32_t)j | code;
-    cnt += in_range(r20, rc2m1) ? 1 : 0;
-    if (cnt > CAP - 2) return j + 1;
+    if (cnt > CAP - U) return j + U;
   }
   return -1;
 }
@@ -112,12 +94,15 @@ struct WarpScratch {
   int start[32];        // lane whose list starts at this chunk position, or -1
 };
 
-template <bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false>
+template <bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false, bool SPREAD = false>
 __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,
                                              int p, bool alive, uint32_t *__restrict__ lst,
-                                             WarpScratch<CAP> *W = nullptr) {
+                                             WarpScratch<CAP> *W = nullptr,
+                                             float4 *__restrict__ own = nullptr) {
+  static_assert(!SPREAD || (HALF && !BAL), "the spread drain serves the half stencil");
   static_assert(CAP >= 4, "list too short");
   constexpr int FLUSH = CAP / 2;
+  constexpr int U = kScanUnroll;
   constexpr int LS = BAL ? 1 : NT;  // list stride: own row of the warp scratch, or a column
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
   if (alive) {
@@ -132,15 +117,18 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
   const uint32_t rc2m1 = __float_as_uint(B.rc2) - 1u;
   const bool k_is_one = (B.kexp == 1.0f);
+  if constexpr (SPREAD) {
+    own[threadIdx.x & 31] = pi;  // w: id bits
+    own[32 + (threadIdx.x & 31)] = vi;
+  }
 
   float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
   int cnt = 0;
 
   // Pair force of one list entry for a target at (qi, ui): F_ij (3) and r . F^C.
-  auto pair = [&](uint32_t e, const float4 &qi, const float4 &ui) -> float4 {
+  auto pair_at = [&](uint32_t e, const float4 &pj, const float4 &vj, const float4 &qi,
+                     const float4 &ui) -> float4 {
     const int j = (int)(e & kSlotMask);
-    const float4 pj = __ldg(P.pos + j);
-    const float4 vj = __ldg(P.vel + j);
     float dx, dy, dz;
     if (e & ~kSlotMask) {  // pair across a box face (rare)
       dx = ((e & kCodeIX) ? qi.x - Lx : qi.x) - ((e & kCodeJX) ? pj.x - Lx : pj.x);
@@ -178,6 +166,10 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
                                  __fmul_rn(fc, r));
     if constexpr (HALF) atomicAdd(P.frc + j, make_float4(-g.x, -g.y, -g.z, g.w));
     return g;
+  };
+  auto pair = [&](uint32_t e, const float4 &qi, const float4 &ui) -> float4 {
+    const int j = (int)(e & kSlotMask);
+    return pair_at(e, __ldg(P.pos + j), __ldg(P.vel + j), qi, ui);
   };
 
   // Balanced drain: the warp's list entries are processed 32 at a time, one
@@ -227,9 +219,52 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     cnt = 0;
   };
 
+  // Spread drain (half stencil): the warp's list entries are processed 32
+  // at a time, one per lane whatever lane owns them; the owner of entry g is
+  // found by a binary search over the lanes' list offsets, and both F_ij on
+  // i and -F_ij on j go to memory as atomic adds (the half stencil's sums
+  // have no fixed order anyway).  Lane o's target and velocity are in
+  // own[o] and own[32 + o].
+  auto drain_spread = [&]() {
+    const int lane = threadIdx.x & 31;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int off = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();  // every lane's list is complete
+    const uint32_t *wl = lst - lane;  // column of the warp's lane 0
+    const int pw = p - lane;          // slot of the warp's lane 0
+    for (int base = 0; base < total; base += 32) {
+      const int g = base + lane;
+      int o = 0;  // last lane whose list starts at or before g
+#pragma unroll
+      for (int s = 16; s >= 1; s >>= 1) {
+        const int t = __shfl_sync(0xffffffffu, off, o + s);
+        if (t <= g) o += s;
+      }
+      const int offo = __shfl_sync(0xffffffffu, off, o);
+      if (g < total) {
+        const uint32_t e = wl[(g - offo) * LS + o];
+        const int j = (int)(e & kSlotMask);
+        const float4 r = pair_at(e, __ldg(P.pos + j), __ldg(P.vel + j), own[o], own[32 + o]);
+        atomicAdd(P.frc + pw + o, r);
+      }
+    }
+    __syncwarp();  // lists may be refilled
+    cnt = 0;
+  };
+
   auto drain = [&]() {
     if constexpr (BAL) {
       drain_balanced();
+      return;
+    }
+    if constexpr (SPREAD) {
+      drain_spread();
       return;
     }
     for (int k = 0; k < cnt; ++k) {
@@ -347,9 +382,9 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       bool more = false;
       if (sg < nseg) {
         const int stop = (c & (kCodeJX | kCodeJY | kCodeJZ))
-                             ? scan_range<true, LS, CAP>(P.pos, j, j1, ax, ay, az, jsx, jsy, jsz,
+                             ? scan_range<true, LS, CAP, U>(P.pos, j, j1, ax, ay, az, jsx, jsy, jsz,
                                                          rc2m1, c, lst, cnt)
-                             : scan_range<false, LS, CAP>(P.pos, j, j1, ax, ay, az, 0.f, 0.f, 0.f,
+                             : scan_range<false, LS, CAP, U>(P.pos, j, j1, ax, ay, az, 0.f, 0.f, 0.f,
                                                           rc2m1, c, lst, cnt);
         if (stop >= 0 && stop < j1) {
           j = stop;  // list nearly full: continue this segment after a drain
@@ -360,7 +395,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
         }
       }
       const bool any_more = __any_sync(0xffffffffu, more);
-      if (__any_sync(0xffffffffu, cnt > CAP - 2) ||
+      if (__any_sync(0xffffffffu, cnt > CAP - U) ||
           (!any_more && __any_sync(0xffffffffu, cnt > FLUSH)))
         drain();
       if (!any_more) break;
@@ -390,11 +425,12 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
 }
 
 // One thread per target slot in [slot0, slot1).
-template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL, bool GAUSS>
+template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL, bool GAUSS, bool SPREAD>
 __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   constexpr int kListWords = BAL ? 1 : CAP * NT;
   __shared__ uint32_t smem_list[kListWords];
   __shared__ WarpScratch<BAL ? CAP : 4> smem_warp[BAL ? NT / 32 : 1];
+  __shared__ float4 smem_own[SPREAD ? 2 * NT : 1];
   const int p = slot0 + blockIdx.x * NT + threadIdx.x;
   bool alive = p < slot1;
   int b = 0;
@@ -406,6 +442,9 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
     WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
     force_direct<HALF, NT, CAP, true, GAUSS>(P, B, S, p, alive,
                                              W->list + (threadIdx.x & 31) * (CAP + 1), W);
+  } else if constexpr (SPREAD) {
+    force_direct<HALF, NT, CAP, false, GAUSS, true>(P, B, S, p, alive, smem_list + threadIdx.x,
+                                                    nullptr, smem_own + (threadIdx.x >> 5) * 64);
   } else {
     force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x);
   }
@@ -703,10 +742,11 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
 struct VariantInfo {
   int threads, cap;
 };
-// Variants 7..9 use the balanced drain.
+// Variants 7..9 use the balanced drain, 10..12 the spread drain (half
+// stencil; with the full stencil they run the per-lane drain).
 static const VariantInfo kVariants[kNumForceVariants] = {
     {128, 24}, {128, 16}, {128, 32}, {256, 24}, {64, 24}, {64, 32}, {256, 32},
-    {64, 24}, {128, 24}, {256, 24}};
+    {64, 24}, {128, 24}, {256, 24}, {64, 32}, {128, 32}, {128, 24}};
 
 int force_variant_info(int v, int *threads, int *cap) {
   if (v < 0 || v >= kNumForceVariants) return -1;
@@ -715,10 +755,12 @@ int force_variant_info(int v, int *threads, int *cap) {
   return 0;
 }
 
-template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false>
+template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false,
+          bool SPREAD = false>
 static void launch_k(const Packed &P, int s0, int s1, cudaStream_t s) {
   if (s1 > s0)
-    k_force<SINGLE, HALF, NT, CAP, BAL, GAUSS><<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
+    k_force<SINGLE, HALF, NT, CAP, BAL, GAUSS, SPREAD && HALF>
+        <<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
 }
 
 template <bool SINGLE, bool HALF>
@@ -737,6 +779,9 @@ static void launch_variant(int v, bool gauss, const Packed &P, int s0, int s1, c
     case 7: launch_k<SINGLE, HALF, 64, 24, true>(P, s0, s1, s); break;
     case 8: launch_k<SINGLE, HALF, 128, 24, true>(P, s0, s1, s); break;
     case 9: launch_k<SINGLE, HALF, 256, 24, true>(P, s0, s1, s); break;
+    case 10: launch_k<SINGLE, HALF, 64, 32, false, false, true>(P, s0, s1, s); break;
+    case 11: launch_k<SINGLE, HALF, 128, 32, false, false, true>(P, s0, s1, s); break;
+    case 12: launch_k<SINGLE, HALF, 128, 24, false, false, true>(P, s0, s1, s); break;
     default: launch_k<SINGLE, HALF, 128, 24>(P, s0, s1, s); break;
   }
 }

@@ -46,7 +46,7 @@ struct ForceBand {
   int gauss;  // 1: some box of the band draws Gaussian noise
 };
 constexpr int kMaxBands = 8;
-constexpr int kNumForceVariants = 10;
+constexpr int kNumForceVariants = 13;
 
 // How a step is launched.
 struct StepConfig {
