@@ -98,7 +98,8 @@ template <bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false, bool
 __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,
                                              int p, bool alive, uint32_t *__restrict__ lst,
                                              WarpScratch<CAP> *W = nullptr,
-                                             float4 *__restrict__ own = nullptr) {
+                                             float4 *__restrict__ own = nullptr,
+                                             bool mixed = false) {
   static_assert(!SPREAD || (HALF && !BAL), "the spread drain serves the half stencil");
   static_assert(CAP >= 4, "list too short");
   constexpr int FLUSH = CAP / 2;
@@ -258,14 +259,21 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     cnt = 0;
   };
 
+  // The balanced and spread drains evaluate entries of other lanes with this
+  // lane's box parameters and step, so a warp whose lanes span two boxes
+  // (`mixed`, warp-uniform) drains per lane.
   auto drain = [&]() {
     if constexpr (BAL) {
-      drain_balanced();
-      return;
+      if (!mixed) {
+        drain_balanced();
+        return;
+      }
     }
     if constexpr (SPREAD) {
-      drain_spread();
-      return;
+      if (!mixed) {
+        drain_spread();
+        return;
+      }
     }
     for (int k = 0; k < cnt; ++k) {
       const float4 g = pair(lst[k * LS], pi, vi);
@@ -438,13 +446,20 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   const BoxDev B = box_of<SINGLE>(P, b);
   const BoxState S = P.st[b];
   alive = alive && S.adv;
+  bool mixed = false;  // live lanes of this warp in more than one box
+  if constexpr (!SINGLE && (BAL || SPREAD)) {
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    mixed = !__all_sync(0xffffffffu, !alive || b == b0);
+  }
   if constexpr (BAL) {
     WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
     force_direct<HALF, NT, CAP, true, GAUSS>(P, B, S, p, alive,
-                                             W->list + (threadIdx.x & 31) * (CAP + 1), W);
+                                             W->list + (threadIdx.x & 31) * (CAP + 1), W,
+                                             nullptr, mixed);
   } else if constexpr (SPREAD) {
     force_direct<HALF, NT, CAP, false, GAUSS, true>(P, B, S, p, alive, smem_list + threadIdx.x,
-                                                    nullptr, smem_own + (threadIdx.x >> 5) * 64);
+                                                    nullptr, smem_own + (threadIdx.x >> 5) * 64,
+                                                    mixed);
   } else {
     force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x);
   }

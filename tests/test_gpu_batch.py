@@ -63,6 +63,40 @@ def test_batch_equals_each_box_alone(mods, stencil):
         assert stats[k]["step"] == nst and stats[k]["n"] == len(x)
 
 
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_batch_every_variant_matches_each_box_alone(mods, stencil):
+    """Every force-kernel variant on a packed mix, where warps straddle box
+    boundaries: the same trajectory and forces as each box alone (bitwise
+    for the full stencil, up to summation order for the half stencil)."""
+    D, B = mods
+    specs, states = _mix(8, seed=6)
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
+             for s, st in zip(specs, states)]
+    alone = [_alone(D, s, x, v, 3, stencil) for s, (x, v) in zip(specs, states)]
+    up0, var0 = B.tuning_get(stencil)
+    try:
+        for variant in range(B.NUM_FORCE_VARIANTS):
+            B.tuning_set(stencil, [1e9], [variant])
+            bt = B.Batch(descs, stencil=stencil)
+            for k, (x, v) in enumerate(states):
+                bt.set_state(k, x, v)
+            bt.step(3)
+            for k, (s, ((xa, va), fa)) in enumerate(zip(specs, alone)):
+                xb, _ = bt.get_state(k)
+                fb = bt.get_forces(k)
+                if stencil == 0:
+                    assert np.array_equal(xa, xb) and np.array_equal(fa, fb), (variant, k)
+                else:
+                    d = xb.astype(np.float64) - xa
+                    d -= s.L * np.round(d / s.L)
+                    rms = np.sqrt((fa.astype(np.float64) ** 2).sum(1).mean())
+                    assert np.abs(d).max() < 1e-5, (variant, k)
+                    assert np.abs(fb.astype(np.float64) - fa).max() < 1e-4 * rms, (variant, k)
+            bt.close()
+    finally:
+        B.tuning_set(stencil, up0, var0)
+
+
 def test_batch_boxes_match_oracle(mods):
     D, B = mods
     specs, states = _mix(6, seed=4)
