@@ -268,8 +268,7 @@ def run_batched(args, stream, world, rank):
             "value": rate_b, "unit": UNIT, "ms_per_step": ms_b / args.batch_steps,
             "one_box_at_a_time": {"value": rate_s, "ms_per_step": ms_s / args.batch_steps},
             "speedup_vs_one_at_a_time": rate_b / rate_s,
-            "stages_ms": {k: round(t, 5) for k, t in zip(dpd.STAGE_NAMES, stage_ms)},
-            "gpu_launches_per_step": dpd.KERNELS_PER_STEP}
+            "stages_ms": {k: round(t, 5) for k, t in zip(dpd.STAGE_NAMES, stage_ms)}}
 
 
 def run_served(args, rank=0, world=1):
@@ -479,7 +478,7 @@ def run_native(args):
                                       f"({clock_src})"},
             "stages": stages,
             "stencils": stencils,
-            "gpu_launches": dpd.KERNELS_PER_STEP * args.steps,
+            "gpu_launches": dpd.kernels_per_step(args.stencil == "half") * args.steps,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": base,

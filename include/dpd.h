@@ -181,7 +181,9 @@ DPD_API int64_t dpd_num_particles(const dpd_ctx *ctx);
 
 /* ------------------------------------------------------- instrumentation */
 #define DPD_NUM_STAGES 5       /* integrate+count, scan, key pass, reorder, force */
-#define DPD_KERNELS_PER_STEP 7 /* kernel launches per step (the scan takes three) */
+#define DPD_KERNELS_PER_STEP 7 /* kernel launches per step of one force band with the full
+                                 * stencil (the scan takes three); the half stencil has no
+                                 * key pass: one fewer */
 
 /* Advance nsteps steps like dpd_step, launching each step's kernels directly
  * (no graph) with CUDA events recorded on the context's stream between the
@@ -203,20 +205,24 @@ DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uin
  * block, pair-list entries per thread and how a warp drains its lists:
  * variants 0-6 per lane, 7-9 balanced over the warp in list order, 10-12
  * spread over the warp with atomic sums (half stencil only; with the full
- * stencil 10-12 drain per lane).  A process-wide table, one per
- * stencil, maps density bands (upper bounds of rho = N/V, increasing; the
- * last band also takes every higher density) to a variant.  Contexts and
- * batches pick their variants from it when their state is laid out, or
- * after dpd_tuning_apply.  The package's autotuner measures the variants
- * per band on the GPU and sets the table. */
+ * stencil 10-12 drain per lane).  Process-wide tables map density bands
+ * (upper bounds of rho = N/V, increasing; the last band also takes every
+ * higher density) to a variant.  There are four: table = stencil
+ * (DPD_STENCIL_FULL/HALF) for a single box, stencil + DPD_TUNING_PACKED
+ * for packed sets of several boxes, whose kernels differ (each lane looks
+ * up its box); a packed table never set uses its stencil's single-box
+ * table.  Contexts and batches pick their variants when their state is
+ * laid out.  The package's autotuner measures the variants per band on the
+ * GPU and sets the tables. */
 #define DPD_NUM_FORCE_VARIANTS 13
 #define DPD_MAX_DENSITY_BANDS 8
+#define DPD_TUNING_PACKED 2
 /* threads per block and list capacity of variant v; DPD_ERR_ARG if out of range */
 DPD_API int dpd_force_variant_info(int v, int *threads, int *list_capacity);
-/* set the table of `stencil` (DPD_STENCIL_FULL/HALF): nbands in 1..DPD_MAX_DENSITY_BANDS */
-DPD_API int dpd_tuning_set(int stencil, int nbands, const double *rho_upper, const int *variant);
-/* copy at most `max` bands of the table; *nbands receives the table's length */
-DPD_API int dpd_tuning_get(int stencil, int max, double *rho_upper, int *variant, int *nbands);
+/* set table 0..3 (see above): nbands in 1..DPD_MAX_DENSITY_BANDS */
+DPD_API int dpd_tuning_set(int table, int nbands, const double *rho_upper, const int *variant);
+/* copy at most `max` bands of the table in use; *nbands receives its length */
+DPD_API int dpd_tuning_get(int table, int max, double *rho_upper, int *variant, int *nbands);
 
 /* ============================================================ many boxes */
 /* A batch steps many independent periodic boxes together: their particles

@@ -11,6 +11,9 @@ import numpy as np
 
 BATCH_GRAPH_CHUNK = 100
 NUM_FORCE_VARIANTS = 13
+TUNING_PACKED = 2
+# tuning tables: single box (full, half stencil) and packed sets of boxes
+TABLES = (("full", 0), ("half", 1), ("full_packed", 2), ("half_packed", 3))
 MAX_DENSITY_BANDS = 8
 TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
@@ -59,7 +62,7 @@ def _load_tuning_file(L):
         return
     with open(TUNING_FILE) as f:
         table = json.load(f)
-    for stencil_name, stencil in (("full", 0), ("half", 1)):
+    for stencil_name, stencil in TABLES:
         bands = table.get(stencil_name)
         if not bands:
             continue
@@ -84,17 +87,18 @@ def variant_info(v: int) -> tuple:
     return t.value, c.value
 
 
-def tuning_set(stencil: int, rho_upper, variants):
+def tuning_set(table: int, rho_upper, variants):
+    """Set tuning table `table`: stencil (0 full, 1 half) + TUNING_PACKED for packed sets."""
     up = (ctypes.c_double * len(rho_upper))(*rho_upper)
     var = (ctypes.c_int * len(variants))(*variants)
-    _check(_lib().dpd_tuning_set(stencil, len(rho_upper), up, var))
+    _check(_lib().dpd_tuning_set(table, len(rho_upper), up, var))
 
 
-def tuning_get(stencil: int):
+def tuning_get(table: int):
     n = ctypes.c_int()
     up = (ctypes.c_double * MAX_DENSITY_BANDS)()
     var = (ctypes.c_int * MAX_DENSITY_BANDS)()
-    _check(_lib().dpd_tuning_get(stencil, MAX_DENSITY_BANDS, up, var, ctypes.byref(n)))
+    _check(_lib().dpd_tuning_get(table, MAX_DENSITY_BANDS, up, var, ctypes.byref(n)))
     return list(up[:n.value]), list(var[:n.value])
 
 

@@ -57,22 +57,22 @@ int dpd_force_variant_info(int v, int *threads, int *list_capacity) {
   return DPD_OK;
 }
 
-int dpd_tuning_set(int stencil, int nbands, const double *rho_upper, const int *variant) {
+int dpd_tuning_set(int table, int nbands, const double *rho_upper, const int *variant) {
   dpd::clear_error();
   if (!rho_upper || !variant) return dpd::set_error(DPD_ERR_ARG, "null argument");
-  if (dpd::tuning_set(stencil, nbands, rho_upper, variant))
+  if (dpd::tuning_set(table, nbands, rho_upper, variant))
     return dpd::set_error(DPD_ERR_ARG,
-                          "bad tuning table (stencil 0/1, 1..%d bands, increasing bounds, "
+                          "bad tuning table (table 0..3, 1..%d bands, increasing bounds, "
                           "variants 0..%d)",
                           DPD_MAX_DENSITY_BANDS, DPD_NUM_FORCE_VARIANTS - 1);
   return DPD_OK;
 }
 
-int dpd_tuning_get(int stencil, int max, double *rho_upper, int *variant, int *nbands) {
+int dpd_tuning_get(int table, int max, double *rho_upper, int *variant, int *nbands) {
   dpd::clear_error();
   if (!nbands) return dpd::set_error(DPD_ERR_ARG, "null argument");
-  const int n = dpd::tuning_get(stencil, max, rho_upper, variant);
-  if (n < 0) return dpd::set_error(DPD_ERR_ARG, "stencil must be 0 or 1");
+  const int n = dpd::tuning_get(table, max, rho_upper, variant);
+  if (n < 0) return dpd::set_error(DPD_ERR_ARG, "table must be 0..3");
   *nbands = n;
   return DPD_OK;
 }
@@ -110,7 +110,7 @@ int dpd_batch_create(dpd_batch **out, int nbox, const dpd_box_desc *descs) {
     n[i] = d.n;
     steps[i] = d.steps > 0 ? d.steps : INT64_MAX / 4;
     const double rho = (double)d.n / (d.box[0] * d.box[1] * d.box[2]);
-    band[i] = dpd::tuned_band(0, rho);
+    band[i] = dpd::tuned_band(DPD_TUNING_PACKED, rho);  // density band of the packed tables
   }
   // pack by density band, keeping the caller's order inside a band
   std::vector<int> order(nbox);

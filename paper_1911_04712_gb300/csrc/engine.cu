@@ -170,7 +170,8 @@ int Engine::build_bands() {
   for (int b = 0; b < nb; ++b) {
     const BoxDev &B = boxes_[b];
     const double rho = (double)B.np / ((double)B.L[0] * B.L[1] * B.L[2]);
-    const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(cfg_.stencil, rho);
+    const int table = cfg_.stencil + (nb > 1 ? 2 : 0);  // packed sets have their own table
+    const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(table, rho);
     const int g = B.noise != 0;
     if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g)
       runs.back().slot1 = pbase_[b + 1];

@@ -443,7 +443,6 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   bool alive = p < slot1;
   int b = 0;
   if constexpr (!SINGLE) b = find_box_warp(P.pbase, P.nbox, min(p, P.ntot - 1));
-  const BoxDev B = box_of<SINGLE>(P, b);
   const BoxState S = P.st[b];
   alive = alive && S.adv;
   bool mixed = false;  // live lanes of this warp in more than one box
@@ -451,17 +450,24 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
     mixed = !__all_sync(0xffffffffu, !alive || b == b0);
   }
-  if constexpr (BAL) {
-    WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
-    force_direct<HALF, NT, CAP, true, GAUSS>(P, B, S, p, alive,
-                                             W->list + (threadIdx.x & 31) * (CAP + 1), W,
-                                             nullptr, mixed);
-  } else if constexpr (SPREAD) {
-    force_direct<HALF, NT, CAP, false, GAUSS, true>(P, B, S, p, alive, smem_list + threadIdx.x,
-                                                    nullptr, smem_own + (threadIdx.x >> 5) * 64,
-                                                    mixed);
+  auto run = [&](const BoxDev &B) {
+    if constexpr (BAL) {
+      WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
+      force_direct<HALF, NT, CAP, true, GAUSS>(P, B, S, p, alive,
+                                               W->list + (threadIdx.x & 31) * (CAP + 1), W,
+                                               nullptr, mixed);
+    } else if constexpr (SPREAD) {
+      force_direct<HALF, NT, CAP, false, GAUSS, true>(P, B, S, p, alive, smem_list + threadIdx.x,
+                                                      nullptr, smem_own + (threadIdx.x >> 5) * 64,
+                                                      mixed);
+    } else {
+      force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x);
+    }
+  };
+  if constexpr (SINGLE) {
+    run(P.single);
   } else {
-    force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x);
+    run(P.boxes[b]);  // read where used from the box table, not copied into registers
   }
 }
 
@@ -848,34 +854,42 @@ cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s)
 }
 
 // ============================================================ tuning table
-// Process-wide map from density band to direct-kernel variant, one per
-// stencil.  Bands are given by increasing upper bounds of rho (particles per
-// rc^3); densities above the last bound use the last band.
+// Process-wide maps from density band to direct-kernel variant: table
+// stencil + 2 * packed, i.e. 0/1 for a single box (full/half stencil) and
+// 2/3 for packed sets of several boxes (whose kernels look up each lane's
+// box and differ in register use).  A packed table that was never set
+// falls back to the single-box table of its stencil.  Bands are given by
+// increasing upper bounds of rho (particles per rc^3); densities above the
+// last bound use the last band.
 namespace {
 struct Tuning {
   std::vector<double> upper;
   std::vector<int> variant;
 };
 std::mutex g_tune_mu;
-Tuning g_tune[2] = {{{1e30}, {0}}, {{1e30}, {0}}};
+Tuning g_tune[4] = {{{1e30}, {0}}, {{1e30}, {0}}, {}, {}};
+
+const Tuning &effective(int table) {  // g_tune_mu held
+  return g_tune[table].upper.empty() ? g_tune[table & 1] : g_tune[table];
+}
 }  // namespace
 
-int tuning_set(int stencil, int n, const double *upper, const int *variant) {
-  if (stencil < 0 || stencil > 1 || n < 1 || n > kMaxBands) return -1;
+int tuning_set(int table, int n, const double *upper, const int *variant) {
+  if (table < 0 || table > 3 || n < 1 || n > kMaxBands) return -1;
   for (int k = 0; k < n; ++k) {
     if (variant[k] < 0 || variant[k] >= kNumForceVariants) return -1;
     if (k > 0 && !(upper[k] > upper[k - 1])) return -1;
   }
   std::lock_guard<std::mutex> g(g_tune_mu);
-  g_tune[stencil].upper.assign(upper, upper + n);
-  g_tune[stencil].variant.assign(variant, variant + n);
+  g_tune[table].upper.assign(upper, upper + n);
+  g_tune[table].variant.assign(variant, variant + n);
   return 0;
 }
 
-int tuning_get(int stencil, int max, double *upper, int *variant) {
-  if (stencil < 0 || stencil > 1) return -1;
+int tuning_get(int table, int max, double *upper, int *variant) {
+  if (table < 0 || table > 3) return -1;
   std::lock_guard<std::mutex> g(g_tune_mu);
-  const Tuning &t = g_tune[stencil];
+  const Tuning &t = effective(table);
   const int n = (int)t.upper.size();
   for (int k = 0; k < n && k < max; ++k) {
     if (upper) upper[k] = t.upper[k];
@@ -884,18 +898,18 @@ int tuning_get(int stencil, int max, double *upper, int *variant) {
   return n;
 }
 
-int tuned_band(int stencil, double rho) {
+int tuned_band(int table, double rho) {
   std::lock_guard<std::mutex> g(g_tune_mu);
-  const Tuning &t = g_tune[stencil == 1 ? 1 : 0];
+  const Tuning &t = effective(table & 3);
   for (size_t k = 0; k < t.upper.size(); ++k)
     if (rho <= t.upper[k]) return (int)k;
   return (int)t.upper.size() - 1;
 }
 
-int tuned_variant(int stencil, double rho) {
-  const int band = tuned_band(stencil, rho);
+int tuned_variant(int table, double rho) {
+  const int band = tuned_band(table, rho);
   std::lock_guard<std::mutex> g(g_tune_mu);
-  return g_tune[stencil == 1 ? 1 : 0].variant[band];
+  return effective(table & 3).variant[band];
 }
 
 }  // namespace dpd

@@ -229,13 +229,22 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_keys(Packed P) {
   P.keyTmp[P.start[P.cellOf[p]] + P.slotIn[p]] = p;
 }
 
+// STABLE: a particle's place in its cell is its rank by previous slot among
+// the cell's particles (listed by k_bin_keys), so the order, and with it the
+// full stencil's sums, are reproducible.  Otherwise (half stencil, whose sums
+// are atomic anyway) it is its arrival rank from the count, as in Sec. 3.2.
+template <bool STABLE>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(Packed P, bool zero_frc) {
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
   if (p >= P.ntot) return;
   const int c = P.cellOf[p];
-  const int s0 = P.start[c], s1 = P.start[c + 1];
-  int rank = 0;
-  for (int t = s0; t < s1; ++t) rank += (P.keyTmp[t] < p) ? 1 : 0;
+  const int s0 = P.start[c];
+  int rank = P.slotIn[p];
+  if constexpr (STABLE) {
+    const int s1 = P.start[c + 1];
+    rank = 0;
+    for (int t = s0; t < s1; ++t) rank += (P.keyTmp[t] < p) ? 1 : 0;
+  }
   const int dst = s0 + rank;
   P.pos[dst] = P.pos2[p];
   P.vel[dst] = P.vel2[p];
@@ -543,8 +552,12 @@ cudaError_t launch_step(const Packed &P, bool move, bool advance, const StepConf
   k_scan_reduce<<<nt, kScanThreads, 0, s>>>(P.count, P.bsum);
   k_scan_bsum<<<1, 1024, 0, s>>>(P.bsum, nt);
   k_scan_apply<<<nt, kScanThreads, 0, s>>>(P, advance);
-  k_bin_keys<<<gb, kBinThreads, 0, s>>>(P);
-  k_bin_scatter<<<gb, kBinThreads, 0, s>>>(P, cfg.stencil == 1);
+  if (cfg.stencil == 1) {
+    k_bin_scatter<false><<<gb, kBinThreads, 0, s>>>(P, true);
+  } else {
+    k_bin_keys<<<gb, kBinThreads, 0, s>>>(P);
+    k_bin_scatter<true><<<gb, kBinThreads, 0, s>>>(P, false);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_force(P, cfg, s);
@@ -567,9 +580,12 @@ cudaError_t launch_step_timed(const Packed &P, const StepConfig &cfg, cudaStream
   k_scan_bsum<<<1, 1024, 0, s>>>(P.bsum, nt);
   k_scan_apply<<<nt, kScanThreads, 0, s>>>(P, true);
   if ((e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
-  k_bin_keys<<<gb, kBinThreads, 0, s>>>(P);
+  if (cfg.stencil != 1) k_bin_keys<<<gb, kBinThreads, 0, s>>>(P);
   if ((e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
-  k_bin_scatter<<<gb, kBinThreads, 0, s>>>(P, cfg.stencil == 1);
+  if (cfg.stencil == 1)
+    k_bin_scatter<false><<<gb, kBinThreads, 0, s>>>(P, true);
+  else
+    k_bin_scatter<true><<<gb, kBinThreads, 0, s>>>(P, false);
   if ((e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_force(P, cfg, s)) != cudaSuccess) return e;

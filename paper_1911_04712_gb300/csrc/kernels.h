@@ -62,10 +62,10 @@ cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s)
 // Direct force-kernel variants (threads per block, pair-list capacity).
 int force_variant_info(int v, int *threads, int *cap);
 // Process-wide tuning table: density band -> variant, per stencil.
-int tuning_set(int stencil, int n, const double *upper, const int *variant);
-int tuning_get(int stencil, int max, double *upper, int *variant);
-int tuned_band(int stencil, double rho);
-int tuned_variant(int stencil, double rho);
+int tuning_set(int table, int n, const double *upper, const int *variant);
+int tuning_get(int table, int max, double *upper, int *variant);
+int tuned_band(int table, double rho);
+int tuned_variant(int table, double rho);
 
 #ifdef __CUDACC__
 // Box constants: the kernel parameter copy for a single box, else from memory.

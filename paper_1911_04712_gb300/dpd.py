@@ -27,6 +27,14 @@ PARAM_NOISE = 12
 NOISE_UNIFORM, NOISE_GAUSSIAN = 0, 1
 STENCIL_FULL, STENCIL_HALF = 0, 1
 NUM_STAGES, KERNELS_PER_STEP = 5, 7
+
+
+def kernels_per_step(half: bool, force_bands: int = 1) -> int:
+    """Kernel launches of one step: the full stencil's sequence has a key pass
+    the half stencil skips, and the force kernel launches once per band."""
+    return KERNELS_PER_STEP - (1 if half else 0) + (force_bands - 1)
+
+
 STAGE_NAMES = ("integrate_bin", "scan", "bin_keys", "bin_scatter", "force")
 
 _NAMES = {ERR_ARG: "DPD_ERR_ARG", ERR_NOMEM: "DPD_ERR_NOMEM", ERR_CUDA: "DPD_ERR_CUDA",

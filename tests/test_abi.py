@@ -67,3 +67,23 @@ def test_product_path_refuses_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(dpd, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         dpd.lib()
+
+
+def test_tuning_tables_need_no_gpu(lib):
+    """Four tables (stencil x single/packed), set and read back on the host;
+    setting one leaves the others alone; bad tables are rejected."""
+    import paper_1911_04712_gb300.batch as B
+    import paper_1911_04712_gb300.dpd as dpd
+    saved = [B.tuning_get(t) for t in range(4)]
+    try:
+        B.tuning_set(3, [4.0, 1e9], [12, 2])
+        B.tuning_set(1, [1e9], [5])
+        assert B.tuning_get(3) == ([4.0, 1e9], [12, 2])
+        assert B.tuning_get(1) == ([1e9], [5])
+        for bad in ((4, [1e9], [0]), (1, [2.0, 1.0], [0, 0]), (0, [1e9], [B.NUM_FORCE_VARIANTS])):
+            with pytest.raises(dpd.DPDError) as ei:
+                B.tuning_set(*bad)
+            assert ei.value.code == dpd.ERR_ARG
+    finally:
+        for t, (up, var) in enumerate(saved):
+            B.tuning_set(t, up, var)

@@ -73,10 +73,11 @@ def test_batch_every_variant_matches_each_box_alone(mods, stencil):
     descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
              for s, st in zip(specs, states)]
     alone = [_alone(D, s, x, v, 3, stencil) for s, (x, v) in zip(specs, states)]
-    up0, var0 = B.tuning_get(stencil)
+    table = stencil + B.TUNING_PACKED
+    up0, var0 = B.tuning_get(table)
     try:
         for variant in range(B.NUM_FORCE_VARIANTS):
-            B.tuning_set(stencil, [1e9], [variant])
+            B.tuning_set(table, [1e9], [variant])
             bt = B.Batch(descs, stencil=stencil)
             for k, (x, v) in enumerate(states):
                 bt.set_state(k, x, v)
@@ -94,7 +95,7 @@ def test_batch_every_variant_matches_each_box_alone(mods, stencil):
                     assert np.abs(fb.astype(np.float64) - fa).max() < 1e-4 * rms, (variant, k)
             bt.close()
     finally:
-        B.tuning_set(stencil, up0, var0)
+        B.tuning_set(table, up0, var0)
 
 
 def test_batch_boxes_match_oracle(mods):
