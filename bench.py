@@ -54,11 +54,16 @@ def force_slots_per_particle(rho: float) -> float:
     return cands * CAND_SLOTS + pairs * PAIR_SLOTS
 
 
-# Algorithmic HBM bytes per particle-step of the streaming stages.
+# Algorithmic HBM bytes per particle-step of the streaming stages.  The
+# full stencil orders each cell by previous slot (key pass + ranked
+# reorder); the half stencil has no key pass and its reorder places by
+# arrival rank and also zeroes the force it accumulates into.
 STAGE_BYTES = {
-    "integrate_bin": 48 + 32 + 8,            # read x, v, f; write x', v', cell, arrival rank
-    "bin_keys": 8 + 4,                       # read cell, rank; write key
-    "bin_scatter": 8 + 32 + 32,              # read cell, x', v'; write x, v
+    "full": {"integrate_bin": 48 + 32 + 8,   # read x, v, f; write x', v', cell, arrival rank
+             "bin_keys": 8 + 4,              # read cell, rank; write key
+             "bin_scatter": 8 + 32 + 32},    # read cell, start, x', v'; write x, v
+    "half": {"integrate_bin": 48 + 32 + 8,
+             "bin_scatter": 12 + 32 + 48},   # read cell, rank, start, x', v'; write x, v, f = 0
 }
 
 
@@ -66,7 +71,7 @@ STAGE_BYTES = {
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/force_direct_L128_rho3.md),
 # valid only while the kernel sources and the tuning table (which picks the
 # variant) hash to the value recorded with it.
-TRAFFIC = {("half", 128.0, 3.0): (391.976e6, "25d23a43b7b8aff0")}
+TRAFFIC = {("half", 128.0, 3.0): (391.591e6, "d2c46d197a53d5ed")}
 KERNEL_SOURCES = ("paper_1911_04712_gb300/csrc/force.cu", "paper_1911_04712_gb300/csrc/dpd_device.cuh",
                   "paper_1911_04712_gb300/csrc/kernels.h", "paper_1911_04712_gb300/tuning_gb300.json")
 
@@ -396,8 +401,8 @@ def run_native(args):
     stages = {}
     for name, t in zip(dpd.STAGE_NAMES, stage_ms):
         d = {"ms": round(t, 5), "share": round(t / sum(stage_ms), 4)}
-        if name in STAGE_BYTES:
-            gbs = STAGE_BYTES[name] * n / (t / 1000.0) / 1e9
+        if name in STAGE_BYTES[args.stencil]:
+            gbs = STAGE_BYTES[args.stencil][name] * n / (t / 1000.0) / 1e9
             d.update({"GB/s": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3)})
         stages[name] = d
 

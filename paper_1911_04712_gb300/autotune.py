@@ -38,7 +38,7 @@ def _time_packed(B, stencil, rho, var, nbox, steps, warmup, seed, stream):
     return ms
 
 
-def tune(L: float = 48.0, steps: int = 10, warmup: int = 3, seed: int = 0, nbox: int = 96,
+def tune(L: float = 80.0, steps: int = 10, warmup: int = 3, seed: int = 0, nbox: int = 96,
          verbose=True) -> dict:
     import torch
 
@@ -92,7 +92,7 @@ def tune(L: float = 48.0, steps: int = 10, warmup: int = 3, seed: int = 0, nbox:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
-    ap.add_argument("--L", type=float, default=48.0)
+    ap.add_argument("--L", type=float, default=80.0)
     ap.add_argument("--steps", type=int, default=10)
     args = ap.parse_args()
     table = tune(args.L, args.steps)
