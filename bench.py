@@ -338,9 +338,11 @@ def run_native(args):
 
     from paper_1911_04712_gb300 import build as _build
     if rank == 0 or world == 1:
-        _build.build()
+        _build.build(philox_rounds=args.philox_rounds)
     if dist:
         dist.barrier()
+    if args.philox_rounds != _build.PHILOX_ROUNDS:   # round-count study: that build instead
+        os.environ["DPD_LIBRARY"] = _build.lib_path(args.philox_rounds)
     import paper_1911_04712_gb300.dpd as dpd
     from paper_1911_04712_gb300.workloads import uniform_box_state
 
@@ -393,7 +395,7 @@ def run_native(args):
     force_ms = stage_ms[4]
     traffic = None
     rec = TRAFFIC.get((args.stencil, float(L), float(rho)))
-    if rec and rec[1] == kernel_hash():
+    if rec and rec[1] == kernel_hash() and args.philox_rounds == 10:
         traffic = rec[0]
     slots = force_slots_per_particle(rho) * n
     achieved = slots / (force_ms / 1000.0) / 1e12
@@ -472,6 +474,7 @@ def run_native(args):
             "config": {"workload": f"dpd_periodic_box_L{L:g}_rho{rho:g}", "particles": n,
                        "L": L, "rho": rho, "a": 25.0, "gamma": 4.5, "kT": 1.0, "dt": 0.005,
                        "stencil": args.stencil, "force_tiles": box.tiling(),
+                       "philox_rounds": dpd.philox_rounds(),
                        "l2": "state larger than L2 "
                        f"({48 * n / 1e6:.0f} MB of float4 x, v, f)",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -524,6 +527,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--philox-rounds", type=int, default=10,
+                    help="noise generator rounds (10; others only for a round-count study)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

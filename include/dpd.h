@@ -71,6 +71,9 @@ DPD_API const char *dpd_last_error(void);
 
 /* Library version string. */
 DPD_API const char *dpd_version(void);
+/* Rounds R of the library's Philox-4x32-R noise generator: 10, unless the
+ * library was built with another count for a round-count study. */
+DPD_API int dpd_philox_rounds(void);
 
 /* ================================================================ one box */
 typedef struct dpd_ctx dpd_ctx;

@@ -13,6 +13,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdpd.so")
+PHILOX_ROUNDS = 10  # the noise generator's round count (Philox-4x32-10)
+
+
+def lib_path(philox_rounds: int = PHILOX_ROUNDS) -> str:
+    """The library file; other round counts (for a round-count study) build beside it."""
+    if philox_rounds == PHILOX_ROUNDS:
+        return LIB
+    return os.path.join(HERE, f"libdpd_r{philox_rounds}.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,11 +48,18 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          philox_rounds: int = PHILOX_ROUNDS) -> str:
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    if not 1 <= philox_rounds <= 16:
+        raise ValueError("Philox round count must be 1..16")
+    lib = lib_path(philox_rounds)
+    bdir = BUILD if philox_rounds == PHILOX_ROUNDS else BUILD + f"_r{philox_rounds}"
+    os.makedirs(bdir, exist_ok=True)
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    if philox_rounds != PHILOX_ROUNDS:
+        flags += [f"-DDPD_PHILOX_ROUNDS={philox_rounds}"]
     if extra:
         flags += extra
     if verbose:
@@ -53,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
             jobs.append([nvcc] + flags + ["-c", src, "-o", obj])
@@ -65,18 +80,20 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl",
                                                               "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    rounds = PHILOX_ROUNDS
+    if "--philox-rounds" in sys.argv:
+        rounds = int(sys.argv[sys.argv.index("--philox-rounds") + 1])
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, philox_rounds=rounds))

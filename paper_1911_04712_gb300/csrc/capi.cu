@@ -26,7 +26,13 @@ extern "C" {
 
 const char *dpd_last_error(void) { return dpd::last_error_text(); }
 
-const char *dpd_version(void) { return "gb300-dpd 0.1 (sm_103a, Philox-4x32-" "10)"; }
+#define DPD_STR2(x) #x
+#define DPD_STR(x) DPD_STR2(x)
+const char *dpd_version(void) {
+  return "gb300-dpd 0.1 (sm_103a, Philox-4x32-" DPD_STR(DPD_PHILOX_ROUNDS) ")";
+}
+
+int dpd_philox_rounds(void) { return DPD_PHILOX_ROUNDS; }
 
 int dpd_create(dpd_ctx **out, const double box[3], double a, double gamma, double kT, double rc,
                double dt, uint64_t seed) {

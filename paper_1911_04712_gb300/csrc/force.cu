@@ -260,8 +260,8 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   };
 
   // The balanced and spread drains evaluate entries of other lanes with this
-  // lane's box parameters and step, so a warp whose lanes span two boxes
-  // (`mixed`, warp-uniform) drains per lane.
+  // lane's box parameters and step, so a warp whose lanes (live or not) span
+  // two boxes (`mixed`, warp-uniform) drains per lane.
   auto drain = [&]() {
     if constexpr (BAL) {
       if (!mixed) {
@@ -445,10 +445,13 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
   if constexpr (!SINGLE) b = find_box_warp(P.pbase, P.nbox, min(p, P.ntot - 1));
   const BoxState S = P.st[b];
   alive = alive && S.adv;
-  bool mixed = false;  // live lanes of this warp in more than one box
+  // Lanes of this warp in more than one box.  Every lane counts, dead ones
+  // too: past the end of a band they belong to the next band's box, and the
+  // balanced and spread drains hand them other lanes' entries.
+  bool mixed = false;
   if constexpr (!SINGLE && (BAL || SPREAD)) {
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
-    mixed = !__all_sync(0xffffffffu, !alive || b == b0);
+    mixed = !__all_sync(0xffffffffu, b == b0);
   }
   auto run = [&](const BoxDev &B) {
     if constexpr (BAL) {

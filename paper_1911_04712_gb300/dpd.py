@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdpd.so")
+# DPD_LIBRARY selects another build of the same library (e.g. another
+# Philox round count); the default is the in-tree libdpd.so.
+LIB_PATH = os.environ.get("DPD_LIBRARY") or os.path.join(HERE, "libdpd.so")
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_STATE, ERR_NUMERIC, ERR_TIMEOUT, ERR_BUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
@@ -125,6 +127,13 @@ def check(rc: int):
 
 def version() -> str:
     return lib().dpd_version().decode()
+
+
+def philox_rounds() -> int:
+    """Rounds of the loaded library's Philox-4x32-R noise generator."""
+    L = lib()
+    L.dpd_philox_rounds.restype = ctypes.c_int
+    return L.dpd_philox_rounds()
 
 
 # ----------------------------------------------------------------- helpers

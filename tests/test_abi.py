@@ -87,3 +87,10 @@ def test_tuning_tables_need_no_gpu(lib):
     finally:
         for t, (up, var) in enumerate(saved):
             B.tuning_set(t, up, var)
+
+
+def test_default_library_is_philox_r10(lib):
+    lib.dpd_philox_rounds.restype = ctypes.c_int
+    assert lib.dpd_philox_rounds() == 10
+    lib.dpd_version.restype = ctypes.c_char_p
+    assert b"Philox-4x32-10" in lib.dpd_version()

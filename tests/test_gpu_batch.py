@@ -56,10 +56,12 @@ def test_batch_equals_each_box_alone(mods, stencil):
         fb = bt.get_forces(k)
         if stencil == 0:
             assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb), k
-        else:   # atomics: same up to summation order
+        else:   # atomics: same up to summation order (measured: ~2e-6 after 45 steps)
             d = xb.astype(np.float64) - xa
             d -= s.L * np.round(d / s.L)
-            assert np.abs(d).max() < 1e-3, k
+            assert np.abs(d).max() < 1e-4, k
+            rms = np.sqrt((fa.astype(np.float64) ** 2).sum(1).mean())
+            assert np.abs(fb.astype(np.float64) - fa).max() < 1e-3 * rms, k
         assert stats[k]["step"] == nst and stats[k]["n"] == len(x)
 
 
@@ -94,6 +96,37 @@ def test_batch_every_variant_matches_each_box_alone(mods, stencil):
                     assert np.abs(d).max() < 1e-5, (variant, k)
                     assert np.abs(fb.astype(np.float64) - fa).max() < 1e-4 * rms, (variant, k)
             bt.close()
+    finally:
+        B.tuning_set(table, up0, var0)
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("variants", [(11, 10, 12), (7, 12, 8), (0, 9, 10), (12, 2, 11)])
+def test_batch_bands_with_different_variants(mods, stencil, variants):
+    """Several force bands, each its own launch with its own variant: the lanes
+    past a band's end belong to the next band's box and must not take part in
+    another box's drain."""
+    D, B = mods
+    specs, states = _mix()
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
+             for s, st in zip(specs, states)]
+    alone = [_alone(D, s, x, v, 2, stencil) for s, (x, v) in zip(specs, states)]
+    table = stencil + B.TUNING_PACKED
+    up0, var0 = B.tuning_get(table)
+    try:
+        B.tuning_set(table, [3.5, 4.5, 1e9], list(variants))   # rho 3 / 4 / 5: three bands
+        bt = B.Batch(descs, stencil=stencil)
+        for k, (x, v) in enumerate(states):
+            bt.set_state(k, x, v)
+        bt.step(2)
+        for k, (s, ((xa, va), fa)) in enumerate(zip(specs, alone)):
+            fb = bt.get_forces(k).astype(np.float64)
+            rms = np.sqrt((fa.astype(np.float64) ** 2).sum(1).mean())
+            if stencil == 0:
+                assert np.array_equal(fb, fa), (variants, k)
+            else:
+                assert np.abs(fb - fa).max() < 1e-4 * rms, (variants, k)
+        bt.close()
     finally:
         B.tuning_set(table, up0, var0)
 
