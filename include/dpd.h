@@ -100,6 +100,13 @@ typedef struct dpd_ctx dpd_ctx;
 
 #define DPD_PARAM_NOISE 12        /* DPD_NOISE_UNIFORM (default) or DPD_NOISE_GAUSSIAN */
 
+#define DPD_PARAM_FUSE 13         /* full stencil: 1 (default) lets each step's force kernel also
+                                     kick, drift and bin every particle for the next step of the
+                                     same dpd_step call (no separate integrate pass, no stored
+                                     force in between); 0 runs them as separate kernels.  Both
+                                     give the same bits.  Off for the half stencil, the staged
+                                     tiles and steps followed by sampling. */
+
 #define DPD_NOISE_UNIFORM 0   /* xi = sqrt(3)(2U - 1): uniform, unit variance, bit-exact on CPU */
 #define DPD_NOISE_GAUSSIAN 1  /* xi Gaussian as Sec. 2.1 states: Box-Muller on words 0 and 1,
                                  sqrt(-2 ln U1) cos(2 pi U2); within rounding of libm */
@@ -259,7 +266,7 @@ DPD_API int dpd_batch_create(dpd_batch **out, int nbox, const dpd_box_desc *desc
 DPD_API int dpd_batch_destroy(dpd_batch *b);
 DPD_API int dpd_batch_set_stream(dpd_batch *b, void *stream);
 /* DPD_PARAM_STENCIL, DPD_PARAM_FORCE_TILES, DPD_PARAM_TILE_CELLS,
- * DPD_PARAM_STAGE_CAP, DPD_PARAM_FORCE_VARIANT, or DPD_BATCH_GRAPH_CHUNK
+ * DPD_PARAM_STAGE_CAP, DPD_PARAM_FORCE_VARIANT, DPD_PARAM_FUSE, or DPD_BATCH_GRAPH_CHUNK
  * (steps per captured graph, >= 1) */
 #define DPD_BATCH_GRAPH_CHUNK 100
 DPD_API int dpd_batch_set_option(dpd_batch *b, int key, double value);

@@ -171,6 +171,9 @@ int dpd_batch_set_option(dpd_batch *b, int key, double value) {
     case DPD_PARAM_FORCE_VARIANT:
       if ((rc = as_int(-1, DPD_NUM_FORCE_VARIANTS - 1, &v))) return rc;
       return b->eng.set_variant(v);
+    case DPD_PARAM_FUSE:
+      if ((rc = as_int(0, 1, &v))) return rc;
+      return b->eng.set_fuse(v != 0);
     case DPD_PARAM_FORCE_TILES:
     case DPD_PARAM_TILE_CELLS:
     case DPD_PARAM_STAGE_CAP: {

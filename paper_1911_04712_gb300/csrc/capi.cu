@@ -127,6 +127,9 @@ int dpd_set_param(dpd_ctx *ctx, int key, double value) {
         return dpd::set_error(DPD_ERR_ARG, "force variant must be -1..%d",
                               DPD_NUM_FORCE_VARIANTS - 1);
       return ctx->eng.set_variant((int)value);
+    case DPD_PARAM_FUSE:
+      if (!(value == 0.0 || value == 1.0)) return dpd::set_error(DPD_ERR_ARG, "fuse must be 0 or 1");
+      return ctx->eng.set_fuse(value != 0.0);
     default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
   }
   if (rc) return rc;
@@ -158,6 +161,7 @@ int dpd_get_param(const dpd_ctx *ctx, int key, double *value) {
     case DPD_PARAM_FORCE_VARIANT:
       *value = (ctx->loaded && cfg.nbands > 0) ? cfg.band[0].variant : ctx->eng.variant_override();
       break;
+    case DPD_PARAM_FUSE: *value = ctx->eng.fuse() ? 1.0 : 0.0; break;
     default: return dpd::set_error(DPD_ERR_ARG, "unknown parameter key %d", key);
   }
   return DPD_OK;

@@ -157,6 +157,19 @@ int Engine::set_variant(int variant) {
   return boxes_.empty() ? DPD_OK : build_bands();
 }
 
+int Engine::set_fuse(bool on) {
+  fuse_ = on;
+  drop_graph();
+  return DPD_OK;
+}
+
+// The force kernel can do the next step's kick/drift/bin only when it owns
+// each particle's whole force (full stencil, direct kernels) and nothing
+// reads the state between the two steps (no sampling).
+bool Engine::fused_steps() const {
+  return fuse_ && cfg_.stencil == 0 && !cfg_.tiles && sample_every_ <= 0;
+}
+
 int Engine::refresh_bands() {
   drop_graph();
   return boxes_.empty() ? DPD_OK : build_bands();
@@ -474,8 +487,9 @@ int Engine::capture_graph() {
   cudaGraph_t g = nullptr;
   DPD_CUDA_TRY(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
+  const bool fz = fused_steps();  // steps inside the chunk fused, the last one plain
   for (int k = 0; k < graph_chunk && e == cudaSuccess; ++k) {
-    e = launch_step(P, true, true, cfg_, cap_);
+    e = launch_step(P, true, true, cfg_, cap_, fz && k > 0, fz && k + 1 < graph_chunk);
     if (e == cudaSuccess && sample_every_ > 0)
       e = launch_sample(P, d_.work, (int)work_.size(), d_wbeg_, d_from_, sample_every_, nbins_,
                         d_spart_, d_acc_, cap_);
@@ -523,8 +537,9 @@ int Engine::step(int64_t nsteps) {
     }
   }
   const Packed P = packed();
+  const bool fz = fused_steps();  // the last step of the call stays plain: read-outs follow
   for (int64_t k = 0; k < left; ++k) {
-    DPD_CUDA_TRY(launch_step(P, true, true, cfg_, stream_));
+    DPD_CUDA_TRY(launch_step(P, true, true, cfg_, stream_, fz && k > 0, fz && k + 1 < left));
     int rc = launch_extra(P, stream_);
     if (rc) return rc;
   }

@@ -73,6 +73,9 @@ class Engine {
   // Direct force-kernel variant: -1 (default) picks per box from the tuning
   // table by density; 0..kNumForceVariants-1 forces one for every box.
   int set_variant(int variant);
+  // Fuse each full-stencil step's next kick/drift/bin into its force kernel.
+  int set_fuse(bool on);
+  bool fuse() const { return fuse_; }
   int variant_override() const { return variant_override_; }
   // Re-derive the per-band variants (after the tuning table changed).
   int refresh_bands();
@@ -158,6 +161,8 @@ class Engine {
   int build_tiles();
   int build_bands();
   int variant_override_ = -1;
+  bool fuse_ = true;
+  bool fused_steps() const;  // fusion applies to this engine's steps now
   std::vector<BoxParams> params_;
   std::vector<BoxDev> boxes_;
   std::vector<int> pbase_;

@@ -99,7 +99,8 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
                                              int p, bool alive, uint32_t *__restrict__ lst,
                                              WarpScratch<CAP> *W = nullptr,
                                              float4 *__restrict__ own = nullptr,
-                                             bool mixed = false) {
+                                             bool mixed = false, bool fuse = false,
+                                             bool real = false) {
   static_assert(!SPREAD || (HALF && !BAL), "the spread drain serves the half stencil");
   static_assert(CAP >= 4, "list too short");
   constexpr int FLUSH = CAP / 2;
@@ -411,7 +412,11 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   }
   drain();
 
-  if (!alive) return;
+  if (!alive) {
+    // fused step, box not advanced: the next step only bins this slot
+    if (!HALF && fuse && real) integrate_one(P, B, p, P.pos[p], P.vel[p], 0.f, 0.f, 0.f, false, false);
+    return;
+  }
   if (B.fb_mode != 0) {  // body force (Sec. 4.2 periodic Poiseuille, or constant)
     float add = B.fb;
     if (B.fb_mode == 2) {
@@ -427,6 +432,13 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   }
   if constexpr (HALF) {
     atomicAdd(P.frc + p, make_float4(fx, fy, fz, vir));
+  } else if (fuse) {
+    // the full stencil's force on p is complete here: the next step's row a1
+    // for p, instead of storing the force for a separate integrate pass.  A
+    // box that stops after this step keeps its force for later read-outs.
+    const bool moves = S.remaining > 0;
+    integrate_one(P, B, p, pi, vi, fx, fy, fz, moves, true);
+    if (!moves) P.frc[p] = make_float4(fx, fy, fz, vir);
   } else {
     P.frc[p] = make_float4(fx, fy, fz, vir);
   }
@@ -434,13 +446,14 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
 
 // One thread per target slot in [slot0, slot1).
 template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL, bool GAUSS, bool SPREAD>
-__global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
+__global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1, bool fuse) {
   constexpr int kListWords = BAL ? 1 : CAP * NT;
   __shared__ uint32_t smem_list[kListWords];
   __shared__ WarpScratch<BAL ? CAP : 4> smem_warp[BAL ? NT / 32 : 1];
   __shared__ float4 smem_own[SPREAD ? 2 * NT : 1];
   const int p = slot0 + blockIdx.x * NT + threadIdx.x;
-  bool alive = p < slot1;
+  const bool real = p < slot1;
+  bool alive = real;
   int b = 0;
   if constexpr (!SINGLE) b = find_box_warp(P.pbase, P.nbox, min(p, P.ntot - 1));
   const BoxState S = P.st[b];
@@ -458,13 +471,14 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1) {
       WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
       force_direct<HALF, NT, CAP, true, GAUSS>(P, B, S, p, alive,
                                                W->list + (threadIdx.x & 31) * (CAP + 1), W,
-                                               nullptr, mixed);
+                                               nullptr, mixed, fuse, real);
     } else if constexpr (SPREAD) {
       force_direct<HALF, NT, CAP, false, GAUSS, true>(P, B, S, p, alive, smem_list + threadIdx.x,
                                                       nullptr, smem_own + (threadIdx.x >> 5) * 64,
-                                                      mixed);
+                                                      mixed, fuse, real);
     } else {
-      force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x);
+      force_direct<HALF, NT, CAP, false, GAUSS>(P, B, S, p, alive, smem_list + threadIdx.x,
+                                                nullptr, nullptr, false, fuse, real);
     }
   };
   if constexpr (SINGLE) {
@@ -781,32 +795,33 @@ int force_variant_info(int v, int *threads, int *cap) {
 
 template <bool SINGLE, bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false,
           bool SPREAD = false>
-static void launch_k(const Packed &P, int s0, int s1, cudaStream_t s) {
+static void launch_k(const Packed &P, int s0, int s1, bool fuse, cudaStream_t s) {
   if (s1 > s0)
     k_force<SINGLE, HALF, NT, CAP, BAL, GAUSS, SPREAD && HALF>
-        <<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1);
+        <<<blocks_for(s1 - s0, NT), NT, 0, s>>>(P, s0, s1, fuse);
 }
 
 template <bool SINGLE, bool HALF>
-static void launch_variant(int v, bool gauss, const Packed &P, int s0, int s1, cudaStream_t s) {
+static void launch_variant(int v, bool gauss, const Packed &P, int s0, int s1, bool fuse,
+                           cudaStream_t s) {
   if (gauss) {  // one configuration serves bands that hold Gaussian-noise boxes
-    launch_k<SINGLE, HALF, 128, 24, false, true>(P, s0, s1, s);
+    launch_k<SINGLE, HALF, 128, 24, false, true>(P, s0, s1, fuse, s);
     return;
   }
   switch (v) {
-    case 1: launch_k<SINGLE, HALF, 128, 16>(P, s0, s1, s); break;
-    case 2: launch_k<SINGLE, HALF, 128, 32>(P, s0, s1, s); break;
-    case 3: launch_k<SINGLE, HALF, 256, 24>(P, s0, s1, s); break;
-    case 4: launch_k<SINGLE, HALF, 64, 24>(P, s0, s1, s); break;
-    case 5: launch_k<SINGLE, HALF, 64, 32>(P, s0, s1, s); break;
-    case 6: launch_k<SINGLE, HALF, 256, 32>(P, s0, s1, s); break;
-    case 7: launch_k<SINGLE, HALF, 64, 24, true>(P, s0, s1, s); break;
-    case 8: launch_k<SINGLE, HALF, 128, 24, true>(P, s0, s1, s); break;
-    case 9: launch_k<SINGLE, HALF, 256, 24, true>(P, s0, s1, s); break;
-    case 10: launch_k<SINGLE, HALF, 64, 32, false, false, true>(P, s0, s1, s); break;
-    case 11: launch_k<SINGLE, HALF, 128, 32, false, false, true>(P, s0, s1, s); break;
-    case 12: launch_k<SINGLE, HALF, 128, 24, false, false, true>(P, s0, s1, s); break;
-    default: launch_k<SINGLE, HALF, 128, 24>(P, s0, s1, s); break;
+    case 1: launch_k<SINGLE, HALF, 128, 16>(P, s0, s1, fuse, s); break;
+    case 2: launch_k<SINGLE, HALF, 128, 32>(P, s0, s1, fuse, s); break;
+    case 3: launch_k<SINGLE, HALF, 256, 24>(P, s0, s1, fuse, s); break;
+    case 4: launch_k<SINGLE, HALF, 64, 24>(P, s0, s1, fuse, s); break;
+    case 5: launch_k<SINGLE, HALF, 64, 32>(P, s0, s1, fuse, s); break;
+    case 6: launch_k<SINGLE, HALF, 256, 32>(P, s0, s1, fuse, s); break;
+    case 7: launch_k<SINGLE, HALF, 64, 24, true>(P, s0, s1, fuse, s); break;
+    case 8: launch_k<SINGLE, HALF, 128, 24, true>(P, s0, s1, fuse, s); break;
+    case 9: launch_k<SINGLE, HALF, 256, 24, true>(P, s0, s1, fuse, s); break;
+    case 10: launch_k<SINGLE, HALF, 64, 32, false, false, true>(P, s0, s1, fuse, s); break;
+    case 11: launch_k<SINGLE, HALF, 128, 32, false, false, true>(P, s0, s1, fuse, s); break;
+    case 12: launch_k<SINGLE, HALF, 128, 24, false, false, true>(P, s0, s1, fuse, s); break;
+    default: launch_k<SINGLE, HALF, 128, 24>(P, s0, s1, fuse, s); break;
   }
 }
 
@@ -825,10 +840,12 @@ cudaError_t prepare_device() {
                               maxb);
 }
 
-cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s) {
+cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s, bool fuse) {
   const bool single = (P.nbox == 1);
   const bool half = (cfg.stencil == 1);
+  if (fuse && half) return cudaErrorInvalidValue;  // the half stencil's forces end in atomics
   if (!half && cfg.tiles && cfg.grid.ntiles > 0) {
+    if (fuse) return cudaErrorInvalidValue;  // the staged tiles store forces only
     const size_t smem = tile_smem_bytes(cfg.grid.stage_cap);
     if (single)
       k_force_tiles<true><<<cfg.grid.ntiles, kTileThreads, smem, s>>>(P, cfg.grid);
@@ -843,14 +860,14 @@ cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s)
     const ForceBand &b = bands[k];
     if (single) {
       if (half)
-        launch_variant<true, true>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
+        launch_variant<true, true>(b.variant, b.gauss, P, b.slot0, b.slot1, false, s);
       else
-        launch_variant<true, false>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
+        launch_variant<true, false>(b.variant, b.gauss, P, b.slot0, b.slot1, fuse, s);
     } else {
       if (half)
-        launch_variant<false, true>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
+        launch_variant<false, true>(b.variant, b.gauss, P, b.slot0, b.slot1, false, s);
       else
-        launch_variant<false, false>(b.variant, b.gauss, P, b.slot0, b.slot1, s);
+        launch_variant<false, false>(b.variant, b.gauss, P, b.slot0, b.slot1, fuse, s);
     }
   }
   return cudaGetLastError();

@@ -53,13 +53,6 @@ __global__ void k_load(Packed P, int slot0, int n, const float *__restrict__ pos
 }
 
 // ------------------------------------------------------- integrate + count
-// Full periodic fold for a coordinate that left [0, L) by more than one edge.
-__device__ __forceinline__ float refold(float x, float L) {
-  if (x >= 0.0f && x < L) return x;
-  x = x - L * floorf(x / L);
-  return (x >= 0.0f && x < L) ? x : 0.0f;
-}
-
 template <bool SINGLE>
 __global__ void __launch_bounds__(kBinThreads) k_integrate_bin(Packed P, bool move) {
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
@@ -67,47 +60,9 @@ __global__ void __launch_bounds__(kBinThreads) k_integrate_bin(Packed P, bool mo
   if constexpr (!SINGLE) b = find_box_warp(P.pbase, P.nbox, min(p, P.ntot - 1));
   if (p >= P.ntot) return;
   const BoxDev B = box_of<SINGLE>(P, b);
-  float4 x = P.pos[p];
-  float4 v = P.vel[p];
-  if (move && P.st[b].remaining > 0) {
-    const float4 f = P.frc[p];
-    const float h = B.hdt_m;
-    if (P.st[b].pending) {  // second half kick of the previous step
-      v.x = fmaf(h, f.x, v.x);
-      v.y = fmaf(h, f.y, v.y);
-      v.z = fmaf(h, f.z, v.z);
-    }
-    v.x = fmaf(h, f.x, v.x);  // first half kick of this step
-    v.y = fmaf(h, f.y, v.y);
-    v.z = fmaf(h, f.z, v.z);
-    x.x = wrap_coord(fmaf(B.dt, v.x, x.x), B.L[0]);
-    x.y = wrap_coord(fmaf(B.dt, v.y, x.y), B.L[1]);
-    x.z = wrap_coord(fmaf(B.dt, v.z, x.z), B.L[2]);
-    const bool finite = isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
-                        isfinite(v.y) && isfinite(v.z);
-    if (!finite) {
-      atomicOr(P.err, kErrNonFinite);
-      x.x = isfinite(x.x) ? x.x : 0.0f;
-      x.y = isfinite(x.y) ? x.y : 0.0f;
-      x.z = isfinite(x.z) ? x.z : 0.0f;
-    }
-    if (!(x.x >= 0.0f && x.x < B.L[0] && x.y >= 0.0f && x.y < B.L[1] && x.z >= 0.0f &&
-          x.z < B.L[2])) {
-      atomicOr(P.err, kErrRunaway);  // moved more than one edge in a step
-      x.x = refold(x.x, B.L[0]);
-      x.y = refold(x.y, B.L[1]);
-      x.z = refold(x.z, B.L[2]);
-    }
-  }
-  const int cx = cell_axis(x.x, B.invh[0], B.n[0]);
-  const int cy = cell_axis(x.y, B.invh[1], B.n[1]);
-  const int cz = cell_axis(x.z, B.invh[2], B.n[2]);
-  const int c = B.cellBase + (cz * B.n[1] + cy) * B.n[0] + cx;
-  v.w = __int_as_float(pack_cell(cx, cy, cz));
-  P.pos2[p] = x;
-  P.vel2[p] = v;
-  P.cellOf[p] = c;
-  P.slotIn[p] = atomicAdd(P.count + c, 1);
+  const bool mv = move && P.st[b].remaining > 0;
+  const float4 f = mv ? P.frc[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  integrate_one(P, B, p, P.pos[p], P.vel[p], f.x, f.y, f.z, mv, P.st[b].pending != 0);
 }
 
 // ------------------------------------------------------------------ scan
@@ -540,14 +495,17 @@ cudaError_t launch_load(const Packed &P, int slot0, int n, const float *pos3, co
 }
 
 cudaError_t launch_step(const Packed &P, bool move, bool advance, const StepConfig &cfg,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool fused_in, bool fuse_out) {
   if (P.ntot <= 0) return cudaSuccess;
   const bool single = (P.nbox == 1);
   const int gb = blocks_for(P.ntot, kBinThreads);
-  if (single)
+  if (fused_in) {
+    // row a1 of this step ran in the previous step's force kernel
+  } else if (single) {
     k_integrate_bin<true><<<gb, kBinThreads, 0, s>>>(P, move);
-  else
+  } else {
     k_integrate_bin<false><<<gb, kBinThreads, 0, s>>>(P, move);
+  }
   const int nt = scan_tiles(P.ncell);
   k_scan_reduce<<<nt, kScanThreads, 0, s>>>(P.count, P.bsum);
   k_scan_bsum<<<1, 1024, 0, s>>>(P.bsum, nt);
@@ -560,7 +518,7 @@ cudaError_t launch_step(const Packed &P, bool move, bool advance, const StepConf
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_force(P, cfg, s);
+  return launch_force(P, cfg, s, fuse_out && cfg.stencil == 0);
 }
 
 cudaError_t launch_step_timed(const Packed &P, const StepConfig &cfg, cudaStream_t s,

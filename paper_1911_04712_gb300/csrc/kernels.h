@@ -57,7 +57,10 @@ struct StepConfig {
   ForceBand band[kMaxBands]{};
 };
 size_t tile_smem_bytes(int stage_cap);
-cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s);
+// fuse: full stencil only; the kernel also performs the next step's row a1
+// (integrate_one) for every slot and stores no force.
+cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s,
+                         bool fuse = false);
 
 // Direct force-kernel variants (threads per block, pair-list capacity).
 int force_variant_info(int v, int *threads, int *cap);
@@ -68,6 +71,63 @@ int tuned_band(int table, double rho);
 int tuned_variant(int table, double rho);
 
 #ifdef __CUDACC__
+// Full periodic fold for a coordinate that left [0, L) by more than one edge.
+__device__ __forceinline__ float refold(float x, float L) {
+  if (x >= 0.0f && x < L) return x;
+  x = x - L * floorf(x / L);
+  return (x >= 0.0f && x < L) ? x : 0.0f;
+}
+
+// Row a1 for the particle in slot p (Sec. 3.1 item 5, Eq. 1; Sec. 3.2): if
+// `move`, the second half kick of the previous step (when `pending`), this
+// step's first half kick with the force (fx, fy, fz), the drift and the
+// periodic wrap; then the cell of the position, its arrival rank by an
+// atomic count, and the copies the reorder reads.  The integrate kernel and
+// the full stencil's fused force epilogue both call it, so they give the
+// same bits.
+__device__ __forceinline__ void integrate_one(const Packed &P, const BoxDev &B, int p, float4 x,
+                                              float4 v, float fx, float fy, float fz, bool move,
+                                              bool pending) {
+  if (move) {
+    const float h = B.hdt_m;
+    if (pending) {  // second half kick of the previous step
+      v.x = fmaf(h, fx, v.x);
+      v.y = fmaf(h, fy, v.y);
+      v.z = fmaf(h, fz, v.z);
+    }
+    v.x = fmaf(h, fx, v.x);  // first half kick of this step
+    v.y = fmaf(h, fy, v.y);
+    v.z = fmaf(h, fz, v.z);
+    x.x = wrap_coord(fmaf(B.dt, v.x, x.x), B.L[0]);
+    x.y = wrap_coord(fmaf(B.dt, v.y, x.y), B.L[1]);
+    x.z = wrap_coord(fmaf(B.dt, v.z, x.z), B.L[2]);
+    const bool finite = isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) &&
+                        isfinite(v.y) && isfinite(v.z);
+    if (!finite) {
+      atomicOr(P.err, kErrNonFinite);
+      x.x = isfinite(x.x) ? x.x : 0.0f;
+      x.y = isfinite(x.y) ? x.y : 0.0f;
+      x.z = isfinite(x.z) ? x.z : 0.0f;
+    }
+    if (!(x.x >= 0.0f && x.x < B.L[0] && x.y >= 0.0f && x.y < B.L[1] && x.z >= 0.0f &&
+          x.z < B.L[2])) {
+      atomicOr(P.err, kErrRunaway);  // moved more than one edge in a step
+      x.x = refold(x.x, B.L[0]);
+      x.y = refold(x.y, B.L[1]);
+      x.z = refold(x.z, B.L[2]);
+    }
+  }
+  const int cx = cell_axis(x.x, B.invh[0], B.n[0]);
+  const int cy = cell_axis(x.y, B.invh[1], B.n[1]);
+  const int cz = cell_axis(x.z, B.invh[2], B.n[2]);
+  const int c = B.cellBase + (cz * B.n[1] + cy) * B.n[0] + cx;
+  v.w = __int_as_float(pack_cell(cx, cy, cz));
+  P.pos2[p] = x;
+  P.vel2[p] = v;
+  P.cellOf[p] = c;
+  P.slotIn[p] = atomicAdd(P.count + c, 1);
+}
+
 // Box constants: the kernel parameter copy for a single box, else from memory.
 template <bool SINGLE>
 __device__ __forceinline__ BoxDev box_of(const Packed &P, int b) {
@@ -100,9 +160,12 @@ cudaError_t launch_load(const Packed &P, int box_slot0, int n, const float *pos3
                         float Lx, float Ly, float Lz, cudaStream_t s);
 
 // One step (move = true) or the initial rebuild (move = false):
-// kick/drift/wrap + cell count, scan, reorder, force.
+// kick/drift/wrap + cell count, scan, reorder, force.  fused_in: the previous
+// step's force kernel already did this step's kick/drift/wrap + count, so the
+// step starts at the scan; fuse_out: this step's force kernel does the next
+// step's (full stencil).
 cudaError_t launch_step(const Packed &P, bool move, bool advance, const StepConfig &cfg,
-                        cudaStream_t s);
+                        cudaStream_t s, bool fused_in = false, bool fuse_out = false);
 
 // One step with events recorded around its stages: ev[0] before the
 // integrate/count kernel, then after it, after the scan, after the key pass,

@@ -26,6 +26,7 @@ PARAM_KEXP, PARAM_MASS, PARAM_BODYFORCE, PARAM_POISEUILLE_F = 1, 2, 3, 4
 PARAM_FLOW_AXIS, PARAM_GRAD_AXIS, PARAM_STENCIL = 5, 6, 7
 PARAM_FORCE_TILES, PARAM_TILE_CELLS, PARAM_STAGE_CAP, PARAM_FORCE_VARIANT = 8, 9, 10, 11
 PARAM_NOISE = 12
+PARAM_FUSE = 13
 NOISE_UNIFORM, NOISE_GAUSSIAN = 0, 1
 STENCIL_FULL, STENCIL_HALF = 0, 1
 NUM_STAGES, KERNELS_PER_STEP = 5, 7

@@ -131,6 +131,31 @@ def test_batch_bands_with_different_variants(mods, stencil, variants):
         B.tuning_set(table, up0, var0)
 
 
+def test_batch_fused_integrate_with_step_limits(mods):
+    """Full stencil, packed boxes of which some stop mid-chunk (their step
+    limits): fused and unfused steps give the same bits."""
+    D, B = mods
+    specs, states = _mix(7, seed=8)
+    limits = [0, 5, 33, 0, 64, 1, 40]
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed,
+                         steps=lim) for s, st, lim in zip(specs, states, limits)]
+    outs = []
+    for fuse in (1, 0):
+        bt = B.Batch(descs, stencil=0)
+        bt.set_option(D.PARAM_FUSE, fuse)
+        for k, (x, v) in enumerate(states):
+            bt.set_state(k, x, v)
+        bt.step(50)
+        bt.step(20)
+        outs.append([(bt.get_state(k), bt.get_forces(k)) for k in range(len(specs))])
+        st = bt.stats()
+        for k, lim in enumerate(limits):
+            assert st[k]["step"] == (70 if lim == 0 else min(lim, 70))
+        bt.close()
+    for ((xa, va), fa), ((xb, vb), fb) in zip(*outs):
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+
+
 def test_batch_boxes_match_oracle(mods):
     D, B = mods
     specs, states = _mix(6, seed=4)

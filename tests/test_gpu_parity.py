@@ -244,6 +244,29 @@ def test_full_stencil_is_bitwise_reproducible_and_graph_equals_direct(dpd):
         assert np.array_equal(xg, outs[0][0]) and np.array_equal(vg, outs[0][1])
 
 
+@pytest.mark.parametrize("body", [False, True])
+def test_fused_integrate_gives_the_same_bits(dpd, body):
+    """Full stencil: the force kernel doing the next step's kick, drift and
+    binning (default) against separate kernels: identical state, forces and
+    statistics after graph chunks and direct steps."""
+    L = (7.0, 8.5, 6.25)
+    x, v = uniform_box_state(L, rho=4, seed=21)
+    p = _params(L, seed=21, fb=0.3 if body else 0.0, fb_mode=O.FB_POISEUILLE if body else 0)
+    outs = []
+    for fuse in (1, 0):
+        box = _box(dpd, p)
+        box.set_param(dpd.PARAM_FUSE, fuse)
+        assert box.get_param(dpd.PARAM_FUSE) == fuse
+        box.set_state(x, v)
+        for c in (70, 3, 1):            # two 32-step graphs + 6 direct, then short calls
+            box.step(c)
+        xs, vs = box.get_state()
+        outs.append((xs, vs, box.get_forces(), box.stats()))
+    (x1, v1, f1, s1), (x0, v0, f0, s0) = outs
+    assert np.array_equal(x1, x0) and np.array_equal(v1, v0) and np.array_equal(f1, f0)
+    assert s1["virial"] == s0["virial"] and s1["step"] == s0["step"] == 74
+
+
 def test_device_pointer_io_matches_host(dpd):
     import torch
     L = 6.0
