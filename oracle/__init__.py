@@ -51,6 +51,11 @@ class _Params(ctypes.Structure):
         ("rounds", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("noise", ctypes.c_int),
+        ("nspec", ctypes.c_int),
+        ("species", ctypes.POINTER(ctypes.c_int32)),
+        ("sa", ctypes.c_double * 16),
+        ("sg", ctypes.c_double * 16),
+        ("src", ctypes.c_double * 16),
     ]
 
 
@@ -72,12 +77,39 @@ class Params:
     rounds: int = 10
     seed: int = 0
     noise: int = 0   # 0 uniform, 1 Gaussian
+    # several species: per-pair tables (S x S, symmetric) and the species of
+    # each particle by id; nspec = 1 uses a, gamma, rc
+    nspec: int = 1
+    species: object = None
+    sa: object = None
+    sg: object = None
+    src: object = None
+
+    def set_species(self, species, a, gamma, rc):
+        """Species of each particle (by id) and the S x S interaction tables."""
+        a, gamma, rc = (np.asarray(t, dtype=np.float64) for t in (a, gamma, rc))
+        S = a.shape[0]
+        assert 1 <= S <= 4 and a.shape == gamma.shape == rc.shape == (S, S)
+        self.nspec = S
+        self.species = np.ascontiguousarray(species, dtype=np.int32)
+        pad = lambda t: [float(t[s, u]) if s < S and u < S else 0.0
+                         for s in range(4) for u in range(4)]
+        self.sa, self.sg, self.src = pad(a), pad(gamma), pad(rc)
+        return self
 
     def c(self) -> _Params:
         L = np.broadcast_to(np.asarray(self.L, dtype=np.float64), (3,))
+        zeros = [0.0] * 16
+        sp = None
+        if self.species is not None:
+            self._species_c = np.ascontiguousarray(self.species, dtype=np.int32)
+            sp = self._species_c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         return _Params((ctypes.c_double * 3)(*L), self.a, self.gamma, self.kT, self.rc,
                        self.dt, self.mass, self.kexp, self.fb, self.fb_mode, self.fb_flow,
-                       self.fb_grad, self.rounds, self.seed, self.noise)
+                       self.fb_grad, self.rounds, self.seed, self.noise, self.nspec, sp,
+                       (ctypes.c_double * 16)(*(self.sa or zeros)),
+                       (ctypes.c_double * 16)(*(self.sg or zeros)),
+                       (ctypes.c_double * 16)(*(self.src or zeros)))
 
 
 def build(force: bool = False) -> str:

@@ -25,6 +25,10 @@
  *     velocity predicted at the half step (the fused leapfrog of Sec. 3.1,
  *     item 5) in a periodic box;
  *   - the periodic Poiseuille body force of Sec. 4.2 (or a constant one);
+ *   - several particle species in one box (the particle vectors of Sec. 3.1,
+ *     each pair of species with its own interaction and cut-off): a_st,
+ *     gamma_st and rc_st <= rc from symmetric per-pair tables, the cell list
+ *     built for the largest cut-off rc;
  *   - box statistics: momentum, kinetic energy, kT, virial pressure and a
  *     binned velocity profile.
  *
@@ -56,6 +60,11 @@ typedef struct {
     int rounds;      /* Philox rounds R */
     uint64_t seed;
     int noise;       /* 0: uniform xi = sqrt(3)(2U - 1); 1: Gaussian xi (Box-Muller) */
+    int nspec;       /* species in the box: 1 uses a, gamma, rc above; 2..4 the tables */
+    const int32_t *species;  /* species of the particle with id k is species[k]; NULL: 0 */
+    double sa[16];   /* a_st at [4 s + t] (symmetric) */
+    double sg[16];   /* gamma_st */
+    double src[16];  /* rc_st, at most rc */
 } orc_params;
 
 /* ----------------------------------------------------------------------
@@ -185,15 +194,24 @@ void orc_pair_force(const orc_params *p, const double *xi, const double *xj,
 {
     fij[0] = fij[1] = fij[2] = 0.0;
     if (rfc) *rfc = 0.0;
+    /* interaction of the pair's species (one species: the scalar parameters) */
+    double a = p->a, gamma = p->gamma, rc = p->rc;
+    if (p->nspec > 1) {
+        int si = p->species ? p->species[idi] : 0;
+        int sj = p->species ? p->species[idj] : 0;
+        a = p->sa[4 * si + sj];
+        gamma = p->sg[4 * si + sj];
+        rc = p->src[4 * si + sj];
+    }
     double d[3];
     for (int k = 0; k < 3; ++k) d[k] = min_image(xi[k] - xj[k], p->L[k]);
     double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    if (!(r < p->rc) || r == 0.0) return;
+    if (!(r < rc) || r == 0.0) return;
     double e[3] = {d[0] / r, d[1] / r, d[2] / r};
-    double w = 1.0 - r / p->rc;                       /* Eq. 4 */
+    double w = 1.0 - r / rc;                          /* Eq. 4 */
     double wR = (p->kexp == 1.0) ? w : pow(w, p->kexp);
     double wD = wR * wR;                              /* w_D = w_R^2 */
-    double sigma = sqrt(2.0 * p->gamma * p->kT);      /* sigma^2 = 2 gamma kT */
+    double sigma = sqrt(2.0 * gamma * p->kT);         /* sigma^2 = 2 gamma kT */
     double ev = e[0] * (vi[0] - vj[0]) + e[1] * (vi[1] - vj[1]) + e[2] * (vi[2] - vj[2]);
     double xi_ij;
     if (p->noise == 1) {
@@ -203,8 +221,8 @@ void orc_pair_force(const orc_params *p, const double *xi, const double *xj,
     } else {
         xi_ij = orc_xi_from_word(orc_pair_word(idi, idj, step, p->seed, p->rounds));
     }
-    double FC = p->a * w;                             /* Eq. 3 */
-    double FD = -p->gamma * ev * wD;                  /* Eq. 5, dissipative */
+    double FC = a * w;                                /* Eq. 3 */
+    double FD = -gamma * ev * wD;                     /* Eq. 5, dissipative */
     double FR = sigma * xi_ij * wR / sqrt(p->dt);     /* Eq. 5, random */
     double s = FC + FD + FR;
     for (int k = 0; k < 3; ++k) fij[k] = s * e[k];
