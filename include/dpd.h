@@ -147,6 +147,32 @@ DPD_API int dpd_set_stream(dpd_ctx *ctx, void *stream);
  * n = 0 is allowed.  Errors: DPD_ERR_ARG, DPD_ERR_NOMEM, DPD_ERR_CUDA. */
 DPD_API int dpd_set_state(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel, int where);
 
+/* ------------------------------------------------------------- species */
+/* Several particle species in one box, each pair of species with its own
+ * interaction (the particle vectors of Sec. 3.1, whose pairwise forces may
+ * differ in parameters and cut-off; Sec. 3.2 keeps one cell list per
+ * cut-off, here one list serves all, built for the context's rc).
+ * a, gamma, rc: nspecies x nspecies row-major tables, symmetric, a and gamma
+ * >= 0, 0 < rc_st <= the context's rc; sigma_st^2 = 2 gamma_st kT (Sec. 2.1).
+ * All species share the mass and the weight exponent.  nspecies 2..4
+ * (DPD_MAX_SPECIES); nspecies = 1 returns to one species with the scalar
+ * parameters (the tables may then be NULL).  With a state loaded only the
+ * table values may change, not the count.  The staged force tiles
+ * (DPD_PARAM_FORCE_TILES) serve one species only.  Errors: DPD_ERR_ARG,
+ * DPD_ERR_STATE. */
+#define DPD_MAX_SPECIES 4
+DPD_API int dpd_set_species(dpd_ctx *ctx, int nspecies, const double *a, const double *gamma,
+                            const double *rc);
+/* The species count and, when it is above 1, the tables (nspecies^2 each;
+ * any table pointer may be NULL). */
+DPD_API int dpd_get_species(const dpd_ctx *ctx, int *nspecies, double *a, double *gamma,
+                            double *rc);
+/* dpd_set_state with a species 0..nspecies-1 per particle (int32, in the same
+ * memory as pos and vel; NULL = all species 0); a species out of range is
+ * DPD_ERR_ARG.  n <= 2^26. */
+DPD_API int dpd_set_state_species(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel,
+                                  const int32_t *species, int where);
+
 /* Advance nsteps >= 0 steps.  Asynchronous on the context's stream.
  * Errors: DPD_ERR_STATE before dpd_set_state, DPD_ERR_CUDA. */
 DPD_API int dpd_step(dpd_ctx *ctx, int64_t nsteps);

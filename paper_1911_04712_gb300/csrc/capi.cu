@@ -24,6 +24,8 @@ struct dpd_ctx {
 
 extern "C" {
 
+static_assert(DPD_MAX_SPECIES == dpd::kMaxSpecies, "species limit of the header and the kernels");
+
 const char *dpd_last_error(void) { return dpd::last_error_text(); }
 
 #define DPD_STR2(x) #x
@@ -108,6 +110,8 @@ int dpd_set_param(dpd_ctx *ctx, int key, double value) {
         return dpd::set_error(DPD_ERR_ARG, "tiling parameters are non-negative integers");
       int t = ctx->tiles, c = ctx->tile_cells, cap = ctx->stage_cap;
       if (key == DPD_PARAM_FORCE_TILES) t = (value != 0.0);
+      if (t && ctx->bp.nspec > 1)
+        return dpd::set_error(DPD_ERR_ARG, "the staged force tiles serve one species only");
       if (key == DPD_PARAM_TILE_CELLS) c = (int)value;
       if (key == DPD_PARAM_STAGE_CAP) cap = (int)value;
       rc = ctx->eng.set_tiling(t, c, cap);
@@ -173,23 +177,77 @@ int dpd_set_stream(dpd_ctx *ctx, void *stream) {
   return ctx->eng.set_stream((cudaStream_t)stream);
 }
 
-int dpd_set_state(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel, int where) {
+int dpd_set_state_species(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel,
+                          const int32_t *species, int where) {
   dpd::clear_error();
   if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
-  if (n < 0 || n > (int64_t)(1 << 30)) return dpd::set_error(DPD_ERR_ARG, "bad particle count");
+  if (n < 0 || n > (int64_t)(1 << 26)) return dpd::set_error(DPD_ERR_ARG, "bad particle count");
   if (where != DPD_WHERE_HOST && where != DPD_WHERE_DEVICE)
     return dpd::set_error(DPD_ERR_ARG, "where must be DPD_WHERE_HOST or DPD_WHERE_DEVICE");
   if (n > 0 && (!pos || !vel)) return dpd::set_error(DPD_ERR_ARG, "null position or velocity");
+  if (species && where == DPD_WHERE_HOST)
+    for (int64_t i = 0; i < n; ++i)
+      if (species[i] < 0 || species[i] >= ctx->bp.nspec)
+        return dpd::set_error(DPD_ERR_ARG, "particle %lld: species %d outside 0..%d",
+                              (long long)i, species[i], ctx->bp.nspec - 1);
   ctx->loaded = false;
   int rc = ctx->eng.layout({ctx->bp}, {n});
   if (rc) return rc;
-  rc = ctx->eng.load_box(0, pos, vel, where == DPD_WHERE_DEVICE);
+  rc = ctx->eng.load_box(0, pos, vel, where == DPD_WHERE_DEVICE, species);
   if (rc) return rc;
   ctx->eng.set_box_state(0, 0, INT64_MAX / 4);
   rc = ctx->eng.rebuild();
   if (rc) return rc;
+  if (species && where == DPD_WHERE_DEVICE && (rc = ctx->eng.check_error())) return rc;
   ctx->n = n;
   ctx->loaded = true;
+  return DPD_OK;
+}
+
+int dpd_set_state(dpd_ctx *ctx, int64_t n, const float *pos, const float *vel, int where) {
+  return dpd_set_state_species(ctx, n, pos, vel, nullptr, where);
+}
+
+int dpd_set_species(dpd_ctx *ctx, int nspecies, const double *a, const double *gamma,
+                    const double *rc) {
+  dpd::clear_error();
+  if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
+  if (nspecies < 1 || nspecies > dpd::kMaxSpecies)
+    return dpd::set_error(DPD_ERR_ARG, "species count must be 1..%d", dpd::kMaxSpecies);
+  if (nspecies > 1 && (!a || !gamma || !rc)) return dpd::set_error(DPD_ERR_ARG, "null table");
+  if (ctx->loaded && nspecies != ctx->bp.nspec)
+    return dpd::set_error(DPD_ERR_STATE,
+                          "the species count changes only before dpd_set_state_species");
+  if (nspecies > 1 && ctx->tiles)
+    return dpd::set_error(DPD_ERR_ARG, "the staged force tiles serve one species only");
+  BoxParams bp = ctx->bp;
+  bp.nspec = nspecies;
+  for (int k = 0; k < 16; ++k) bp.sa[k] = bp.sg[k] = bp.src[k] = 0.0;
+  for (int s = 0; s < nspecies && nspecies > 1; ++s)
+    for (int t = 0; t < nspecies; ++t) {
+      bp.sa[4 * s + t] = a[nspecies * s + t];
+      bp.sg[4 * s + t] = gamma[nspecies * s + t];
+      bp.src[4 * s + t] = rc[nspecies * s + t];
+    }
+  int ncell[3];
+  int r = dpd::check_params(bp, ncell);
+  if (r) return r;
+  ctx->bp = bp;
+  if (ctx->loaded) return ctx->eng.update_params({bp});
+  return DPD_OK;
+}
+
+int dpd_get_species(const dpd_ctx *ctx, int *nspecies, double *a, double *gamma, double *rc) {
+  dpd::clear_error();
+  if (!ctx || !nspecies) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  const BoxParams &bp = ctx->bp;
+  *nspecies = bp.nspec;
+  for (int s = 0; s < bp.nspec && bp.nspec > 1; ++s)
+    for (int t = 0; t < bp.nspec; ++t) {
+      if (a) a[bp.nspec * s + t] = bp.sa[4 * s + t];
+      if (gamma) gamma[bp.nspec * s + t] = bp.sg[4 * s + t];
+      if (rc) rc[bp.nspec * s + t] = bp.src[4 * s + t];
+    }
   return DPD_OK;
 }
 
@@ -244,13 +302,15 @@ int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out) {
 
 namespace {
 struct CheckpointHeader {
-  char magic[8];       // "DPDCKPT1"
+  char magic[8];       // "DPDCKPT2"
   int64_t n;
   double box[3], a, gamma, kT, rc, dt;
   uint64_t seed;
   unsigned long long step;
   long long remaining;
   int pending, stencil;
+  int nspec, pad_;
+  double sa[16], sg[16], src[16];
 };
 }  // namespace
 
@@ -267,7 +327,7 @@ int dpd_checkpoint_save(dpd_ctx *ctx, void *buf, int64_t bytes) {
     return dpd::set_error(DPD_ERR_ARG, "buffer of %lld bytes, need %lld", (long long)bytes,
                           (long long)dpd_checkpoint_size(ctx));
   CheckpointHeader h{};
-  std::memcpy(h.magic, "DPDCKPT1", 8);
+  std::memcpy(h.magic, "DPDCKPT2", 8);
   h.n = ctx->n;
   for (int k = 0; k < 3; ++k) h.box[k] = ctx->bp.L[k];
   h.a = ctx->bp.a;
@@ -281,6 +341,10 @@ int dpd_checkpoint_save(dpd_ctx *ctx, void *buf, int64_t bytes) {
   h.remaining = st.remaining;
   h.pending = st.pending;
   h.stencil = ctx->eng.step_config().stencil;
+  h.nspec = ctx->bp.nspec;
+  std::memcpy(h.sa, ctx->bp.sa, sizeof h.sa);
+  std::memcpy(h.sg, ctx->bp.sg, sizeof h.sg);
+  std::memcpy(h.src, ctx->bp.src, sizeof h.src);
   std::memcpy(buf, &h, sizeof h);
   float4 *arr = reinterpret_cast<float4 *>(static_cast<char *>(buf) + sizeof h);
   return ctx->eng.copy_box_raw(0, arr, arr + ctx->n, arr + 2 * ctx->n, true);
@@ -293,11 +357,13 @@ int dpd_checkpoint_load(dpd_ctx *ctx, const void *buf, int64_t bytes) {
     return dpd::set_error(DPD_ERR_ARG, "buffer too small for a checkpoint");
   CheckpointHeader h;
   std::memcpy(&h, buf, sizeof h);
-  if (std::memcmp(h.magic, "DPDCKPT1", 8) != 0)
+  if (std::memcmp(h.magic, "DPDCKPT2", 8) != 0)
     return dpd::set_error(DPD_ERR_STATE, "not a checkpoint");
   const dpd::BoxParams &bp = ctx->bp;
   if (h.box[0] != bp.L[0] || h.box[1] != bp.L[1] || h.box[2] != bp.L[2] || h.a != bp.a ||
-      h.gamma != bp.gamma || h.kT != bp.kT || h.rc != bp.rc || h.dt != bp.dt || h.seed != bp.seed)
+      h.gamma != bp.gamma || h.kT != bp.kT || h.rc != bp.rc || h.dt != bp.dt || h.seed != bp.seed ||
+      h.nspec != bp.nspec || std::memcmp(h.sa, bp.sa, sizeof h.sa) != 0 ||
+      std::memcmp(h.sg, bp.sg, sizeof h.sg) != 0 || std::memcmp(h.src, bp.src, sizeof h.src) != 0)
     return dpd::set_error(DPD_ERR_STATE, "checkpoint was made with other box parameters");
   if (h.n < 0 || bytes < (int64_t)sizeof h + h.n * 3 * (int64_t)sizeof(float4))
     return dpd::set_error(DPD_ERR_ARG, "checkpoint buffer truncated");

@@ -25,12 +25,18 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;  // Weyl key increments
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
+// A particle's id and species share pos.w: id in the low 30 bits (the pair
+// noise uses the id alone), species 0..3 in the top two.
+constexpr int kSpeciesShift = 30;
+constexpr uint32_t kIdMask = (1u << kSpeciesShift) - 1u;
+constexpr int kMaxSpecies = 4;
 constexpr int kCellBits = 10;                 // packed cell coords: 10 bits per axis
 constexpr int kMaxCellsPerAxis = (1 << kCellBits) - 1;
 
 // Error bits raised by kernels into the context's device error word.
 constexpr unsigned kErrNonFinite = 1u;        // a position or velocity is NaN/Inf
 constexpr unsigned kErrRunaway = 2u;          // a particle moved more than one box edge
+constexpr unsigned kErrSpecies = 4u;          // a loaded species outside 0..nspec-1
 
 // Constants of one periodic box (read-only during a step).
 struct BoxDev {
@@ -57,6 +63,15 @@ struct BoxDev {
   uint32_t seed_hi;
   int noise;        // 0: uniform xi of unit variance, 1: Gaussian xi (Box-Muller)
   float sig_g;      // sigma / sqrt(dt): multiplies a Gaussian xi
+  // Several species (nspec 2..4; 1 uses the scalars above): the interaction
+  // of species s with t at [kMaxSpecies s + t].  rc_st <= rc, the cells' cut-off.
+  int nspec;
+  float sp_a[kMaxSpecies * kMaxSpecies];
+  float sp_gamma[kMaxSpecies * kMaxSpecies];
+  float sp_sig[kMaxSpecies * kMaxSpecies];    // as sig, from gamma_st
+  float sp_sig_g[kMaxSpecies * kMaxSpecies];  // as sig_g, from gamma_st
+  float sp_rc2[kMaxSpecies * kMaxSpecies];
+  float sp_inv_rc[kMaxSpecies * kMaxSpecies];
 };
 
 // Mutable per-box step state (device resident so that graphs can replay it).

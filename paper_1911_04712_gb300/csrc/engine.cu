@@ -54,6 +54,19 @@ int check_params(const BoxParams &bp, int n[3]) {
   if (bp.fb_flow < 0 || bp.fb_flow > 2 || bp.fb_grad < 0 || bp.fb_grad > 2)
     return set_error(DPD_ERR_ARG, "body-force axes must be 0, 1 or 2");
   if (bp.noise != 0 && bp.noise != 1) return set_error(DPD_ERR_ARG, "noise must be 0 or 1");
+  if (bp.nspec < 1 || bp.nspec > kMaxSpecies)
+    return set_error(DPD_ERR_ARG, "species count must be 1..%d", kMaxSpecies);
+  for (int s = 0; s < bp.nspec && bp.nspec > 1; ++s)
+    for (int t = 0; t < bp.nspec; ++t) {
+      const int k = 4 * s + t, kt = 4 * t + s;
+      if (bp.sa[k] != bp.sa[kt] || bp.sg[k] != bp.sg[kt] || bp.src[k] != bp.src[kt])
+        return set_error(DPD_ERR_ARG, "species tables must be symmetric (%d, %d)", s, t);
+      if (!nonneg(bp.sa[k]) || !nonneg(bp.sg[k]))
+        return set_error(DPD_ERR_ARG, "species (%d, %d): a and gamma must be >= 0", s, t);
+      if (!(bp.src[k] > 0.0 && bp.src[k] <= bp.rc))
+        return set_error(DPD_ERR_ARG, "species (%d, %d): cut-off must be in (0, rc = %g]", s, t,
+                         bp.rc);
+    }
   return DPD_OK;
 }
 
@@ -87,6 +100,19 @@ BoxDev make_box_dev(const BoxParams &bp, int cellBase, int pbase, int np) {
   d.fb_half = (float)(0.5 * bp.L[bp.fb_grad]);
   d.seed_lo = (uint32_t)(bp.seed & 0xffffffffu);
   d.seed_hi = (uint32_t)(bp.seed >> 32);
+  d.nspec = bp.nspec;
+  for (int k = 0; k < kMaxSpecies * kMaxSpecies; ++k) {
+    const bool multi = bp.nspec > 1;
+    const double a = multi ? bp.sa[k] : bp.a, g = multi ? bp.sg[k] : bp.gamma;
+    const double rc = multi ? bp.src[k] : bp.rc;
+    const double sg = std::sqrt(2.0 * g * bp.kT);  // fluctuation-dissipation, per pair of species
+    d.sp_a[k] = (float)a;
+    d.sp_gamma[k] = (float)g;
+    d.sp_sig[k] = (float)(sg * std::sqrt(3.0) / 16777216.0 / std::sqrt(bp.dt));
+    d.sp_sig_g[k] = (float)(sg / std::sqrt(bp.dt));
+    d.sp_rc2[k] = (float)(rc * rc);
+    d.sp_inv_rc[k] = rc > 0.0 ? (float)(1.0 / rc) : 0.0f;
+  }
   return d;
 }
 
@@ -185,7 +211,7 @@ int Engine::build_bands() {
     const double rho = (double)B.np / ((double)B.L[0] * B.L[1] * B.L[2]);
     const int table = cfg_.stencil + (nb > 1 ? 2 : 0);  // packed sets have their own table
     const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(table, rho);
-    const int g = B.noise != 0;
+    const int g = B.noise != 0 || B.nspec > 1;  // general kernel
     if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g)
       runs.back().slot1 = pbase_[b + 1];
     else
@@ -435,7 +461,8 @@ int Engine::update_params(const std::vector<BoxParams> &params) {
   return DPD_OK;
 }
 
-int Engine::load_box(int box, const float *pos, const float *vel, bool device_ptr) {
+int Engine::load_box(int box, const float *pos, const float *vel, bool device_ptr,
+                     const int32_t *species) {
   if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
   const int n = pbase_[box + 1] - pbase_[box];
   if (n == 0) return DPD_OK;
@@ -449,9 +476,15 @@ int Engine::load_box(int box, const float *pos, const float *vel, bool device_pt
                                  stream_));
     p3 = sp;
     v3 = sv;
+    if (species) {  // host species: through the key scratch, free between steps
+      DPD_CUDA_TRY(cudaMemcpyAsync(d_.keyTmp, species, (size_t)n * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, stream_));
+      species = d_.keyTmp;
+    }
   }
   const BoxDev &B = boxes_[box];
-  DPD_CUDA_TRY(launch_load(packed(), pbase_[box], n, p3, v3, B.L[0], B.L[1], B.L[2], stream_));
+  DPD_CUDA_TRY(launch_load(packed(), pbase_[box], n, p3, v3, B.L[0], B.L[1], B.L[2], stream_,
+                           species, params_[box].nspec));
   return DPD_OK;
 }
 
@@ -594,6 +627,8 @@ int Engine::check_error() {
   DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
   if (h) {
     DPD_CUDA_TRY(cudaMemsetAsync(d_.err, 0, sizeof(unsigned), stream_));
+    if (h & kErrSpecies)
+      return set_error(DPD_ERR_ARG, "a particle species is outside 0..nspec-1");
     return set_error(DPD_ERR_NUMERIC, "device flagged %s%s",
                      (h & kErrNonFinite) ? "non-finite positions/velocities " : "",
                      (h & kErrRunaway) ? "a particle moving more than one box edge per step" : "");

@@ -36,6 +36,10 @@ struct BoxParams {
   int fb_flow, fb_grad;
   uint64_t seed;
   int noise;        // 0 uniform, 1 Gaussian
+  // several species: nspec 2..4 with symmetric tables at [4 s + t]
+  // (1: one species with a, gamma, rc above)
+  int nspec = 1;
+  double sa[16] = {}, sg[16] = {}, src[16] = {};
 };
 
 // Validates the parameters and derives the cell grid; returns DPD_OK or DPD_ERR_ARG.
@@ -88,7 +92,8 @@ class Engine {
   int update_params(const std::vector<BoxParams> &params);
 
   // Load particles of one box (n x 3 host or device arrays).
-  int load_box(int box, const float *pos, const float *vel, bool device_ptr);
+  int load_box(int box, const float *pos, const float *vel, bool device_ptr,
+               const int32_t *species = nullptr);
   // Host mirror of a box's step state; takes effect at the next rebuild().
   void set_box_state(int box, uint64_t step0, int64_t remaining);
   // Cell-list build and force at each box's current step, without moving

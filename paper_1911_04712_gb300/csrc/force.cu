@@ -142,26 +142,42 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       dz = qi.z - pj.z;
     }
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    // interaction parameters; the general kernels also serve boxes of
+    // several species, whose pair of species picks them (and a cut-off
+    // rc_st <= rc that the pair must be inside)
+    float pa = B.a, pgam = B.gamma, psig = B.sig, psig_g = B.sig_g, pinv_rc = B.inv_rc;
+    uint32_t idi_ = __float_as_uint(qi.w), idj_ = __float_as_uint(pj.w);
+    if constexpr (GAUSS) {
+      if (B.nspec > 1) {
+        const int k = (int)((idi_ >> kSpeciesShift) * kMaxSpecies + (idj_ >> kSpeciesShift));
+        if (!(r2 < B.sp_rc2[k])) return make_float4(0.f, 0.f, 0.f, 0.f);
+        pa = B.sp_a[k];
+        pgam = B.sp_gamma[k];
+        psig = B.sp_sig[k];
+        psig_g = B.sp_sig_g[k];
+        pinv_rc = B.sp_inv_rc[k];
+      }
+      idi_ &= kIdMask;  // the pair noise takes the ids alone
+      idj_ &= kIdMask;
+    }
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    const float w = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
+    const float w = fmaxf(fmaf(-r, pinv_rc, 1.0f), 0.0f);
     const float wR = k_is_one ? w : powf(w, B.kexp);
     const float ev = fmaf(dx, ui.x - vj.x, fmaf(dy, ui.y - vj.y, dz * (ui.z - vj.z))) * rinv;
     float fr;  // random term sigma w_R xi / sqrt(dt)
-    if constexpr (GAUSS) {  // kernels for bands holding a box with Gaussian noise
-      const uint2 u = pair_words(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
-                                 B.seed_lo, B.seed_hi);
+    if constexpr (GAUSS) {  // general kernels: Gaussian noise or several species
+      const uint2 u = pair_words(idi_, idj_, slo, shi, B.seed_lo, B.seed_hi);
       if (B.noise == 0)
-        fr = B.sig * wR * noise_int(u.x);
+        fr = psig * wR * noise_int(u.x);
       else
-        fr = B.sig_g * wR * gauss_xi(u.x, u.y);
+        fr = psig_g * wR * gauss_xi(u.x, u.y);
     } else {
-      const uint32_t u = pair_word(__float_as_uint(qi.w), __float_as_uint(pj.w), slo, shi,
-                                   B.seed_lo, B.seed_hi);
-      fr = B.sig * wR * noise_int(u);
+      const uint32_t u = pair_word(idi_, idj_, slo, shi, B.seed_lo, B.seed_hi);
+      fr = psig * wR * noise_int(u);
     }
-    const float fc = B.a * w;
-    const float s = (fr + fmaf(-B.gamma * wR * wR, ev, fc)) * rinv;
+    const float fc = pa * w;
+    const float s = (fr + fmaf(-pgam * wR * wR, ev, fc)) * rinv;
     // rounded products (no fusion into the caller's sums), so that every
     // drain order-preserving variant adds exactly the same terms
     const float4 g = make_float4(__fmul_rn(s, dx), __fmul_rn(s, dy), __fmul_rn(s, dz),

@@ -30,7 +30,8 @@ constexpr float kSqrt3Scale = (float)(1.7320508075688772 / 16777216.0);  // sqrt
 
 // ------------------------------------------------------------------ load
 __global__ void k_load(Packed P, int slot0, int n, const float *__restrict__ pos3,
-                       const float *__restrict__ vel3, float Lx, float Ly, float Lz) {
+                       const float *__restrict__ vel3, float Lx, float Ly, float Lz,
+                       const int32_t *__restrict__ species, int nspec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float x[3] = {pos3[3 * i], pos3[3 * i + 1], pos3[3 * i + 2]};
@@ -48,7 +49,13 @@ __global__ void k_load(Packed P, int slot0, int n, const float *__restrict__ pos
     }
     x[k] = y;
   }
-  P.pos[slot0 + i] = make_float4(x[0], x[1], x[2], __int_as_float(i));
+  int s = species ? species[i] : 0;
+  if (s < 0 || s >= nspec) {
+    atomicOr(P.err, kErrSpecies);
+    s = 0;
+  }
+  P.pos[slot0 + i] =
+      make_float4(x[0], x[1], x[2], __uint_as_float((uint32_t)i | ((uint32_t)s << kSpeciesShift)));
   P.vel[slot0 + i] = make_float4(vel3[3 * i], vel3[3 * i + 1], vel3[3 * i + 2], 0.0f);
 }
 
@@ -257,8 +264,8 @@ __global__ void k_gather(Packed P, int box, int slot0, int n, float *__restrict_
   if (k >= n) return;
   const int p = slot0 + k;
   const float4 x = P.pos[p];
-  const int id = __float_as_int(x.w);
-  if (id < 0 || id >= n) {
+  const int id = (int)(__float_as_uint(x.w) & kIdMask);
+  if (id >= n) {
     atomicOr(P.err, kErrNonFinite);
     return;
   }
@@ -488,9 +495,10 @@ __global__ void k_sample_acc(const StatsWork *__restrict__ work, const int *__re
 // ================================================================ launchers
 
 cudaError_t launch_load(const Packed &P, int slot0, int n, const float *pos3, const float *vel3,
-                        float Lx, float Ly, float Lz, cudaStream_t s) {
+                        float Lx, float Ly, float Lz, cudaStream_t s, const int32_t *species,
+                        int nspec) {
   if (n <= 0) return cudaSuccess;
-  k_load<<<blocks_for(n, 256), 256, 0, s>>>(P, slot0, n, pos3, vel3, Lx, Ly, Lz);
+  k_load<<<blocks_for(n, 256), 256, 0, s>>>(P, slot0, n, pos3, vel3, Lx, Ly, Lz, species, nspec);
   return cudaGetLastError();
 }
 

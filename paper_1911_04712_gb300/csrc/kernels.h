@@ -156,8 +156,10 @@ inline int scan_tiles(int ncell) { return (ncell + 1 + kScanTile - 1) / kScanTil
 cudaError_t prepare_device();
 
 // Convert n x 3 inputs of one box into float4 slots (ids 0..n-1, wrapped).
+// species: n species 0..nspec-1 (device memory), or null for all 0.
 cudaError_t launch_load(const Packed &P, int box_slot0, int n, const float *pos3, const float *vel3,
-                        float Lx, float Ly, float Lz, cudaStream_t s);
+                        float Lx, float Ly, float Lz, cudaStream_t s,
+                        const int32_t *species = nullptr, int nspec = 1);
 
 // One step (move = true) or the initial rebuild (move = false):
 // kick/drift/wrap + cell count, scan, reorder, force.  fused_in: the previous

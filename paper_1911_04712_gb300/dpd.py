@@ -84,6 +84,10 @@ def lib():
     L.dpd_get_param.argtypes = [vp, i32, c.POINTER(dbl)]
     L.dpd_get_param.restype = i32
     L.dpd_set_state.argtypes = [vp, i64, vp, vp, i32]
+    L.dpd_set_state_species.argtypes = [vp, i64, vp, vp, vp, i32]
+    L.dpd_set_species.argtypes = [vp, i32, c.POINTER(dbl), c.POINTER(dbl), c.POINTER(dbl)]
+    L.dpd_get_species.argtypes = [vp, c.POINTER(i32), c.POINTER(dbl), c.POINTER(dbl),
+                                  c.POINTER(dbl)]
     L.dpd_step.argtypes = [vp, i64]
     L.dpd_get_state.argtypes = [vp, vp, vp, i32]
     L.dpd_get_forces.argtypes = [vp, vp, i32]
@@ -102,6 +106,8 @@ def lib():
     L.dpd_forces_noalloc.argtypes = [i64, vp, vp, c.POINTER(dbl), dbl, dbl, dbl, dbl, dbl, u64,
                                      u64, vp, vp]
     L.dpd_forces_noalloc.restype = i32
+    for name in ("dpd_set_state_species", "dpd_set_species", "dpd_get_species"):
+        getattr(L, name).restype = i32
     for name in ("dpd_create", "dpd_destroy", "dpd_set_param", "dpd_set_stream", "dpd_set_state",
                  "dpd_step", "dpd_get_state", "dpd_get_forces", "dpd_get_stats",
                  "dpd_debug_rng"):
@@ -124,6 +130,11 @@ def check(rc: int):
     if rc != OK:
         raise DPDError(rc, lib().dpd_last_error().decode(errors="replace"))
     return rc
+
+
+def _torch_int32():
+    import torch
+    return torch.int32
 
 
 def version() -> str:
@@ -226,14 +237,55 @@ class Box:
         check(lib().dpd_set_stream(self._ctx, _stream_ptr(stream)))
         self._stream_ref = stream   # the stream must outlive the work enqueued on it
 
-    def set_state(self, pos, vel):
+    def set_state(self, pos, vel, species=None):
+        """Load n particles (ids 0..n-1); species: n ints 0..nspecies-1, in the same
+        memory as pos and vel (NumPy, or a CUDA int32 tensor), or None for all 0."""
         n = int(pos.shape[0])
         pp, wp, kp = _vec3_arg(pos, n)
         vv, wv, kv = _vec3_arg(vel, n)
         if wp != wv:
             raise ValueError("pos and vel must both be host arrays or both CUDA tensors")
-        check(lib().dpd_set_state(self._ctx, n, pp, vv, wp))
+        if species is None:
+            check(lib().dpd_set_state(self._ctx, n, pp, vv, wp))
+        else:
+            if _is_cuda_tensor(species):
+                if wp != WHERE_DEVICE or species.dtype != _torch_int32() or species.numel() != n:
+                    raise ValueError("species must be a CUDA int32 tensor of n entries")
+                keep = species.contiguous()
+                sp = ctypes.c_void_p(keep.data_ptr())
+            else:
+                if wp != WHERE_HOST:
+                    raise ValueError("species must be in the same memory as pos and vel")
+                keep = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
+                if keep.size != n:
+                    raise ValueError("species must have one entry per particle")
+                sp = keep.ctypes.data_as(ctypes.c_void_p)
+            check(lib().dpd_set_state_species(self._ctx, n, pp, vv, sp, wp))
         self.n = n
+
+    def set_species(self, a=None, gamma=None, rc=None):
+        """Interaction tables of several species (S x S, symmetric), or no
+        argument to return to one species."""
+        if a is None:
+            check(lib().dpd_set_species(self._ctx, 1, None, None, None))
+            return
+        t = [np.ascontiguousarray(x, dtype=np.float64) for x in (a, gamma, rc)]
+        S = t[0].shape[0]
+        if any(x.shape != (S, S) for x in t):
+            raise ValueError("a, gamma and rc must be S x S")
+        ptr = [x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for x in t]
+        check(lib().dpd_set_species(self._ctx, S, *ptr))
+
+    def get_species(self):
+        """(S, a, gamma, rc) with S x S tables (None when S is 1)."""
+        S = ctypes.c_int()
+        check(lib().dpd_get_species(self._ctx, ctypes.byref(S), None, None, None))
+        if S.value == 1:
+            return 1, None, None, None
+        t = [np.zeros((S.value, S.value)) for _ in range(3)]
+        ptr = [x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for x in t]
+        check(lib().dpd_get_species(self._ctx, ctypes.byref(S), *ptr))
+        return (S.value, *t)
 
     def step(self, nsteps: int = 1):
         check(lib().dpd_step(self._ctx, int(nsteps)))

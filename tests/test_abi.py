@@ -94,3 +94,4 @@ def test_default_library_is_philox_r10(lib):
     assert lib.dpd_philox_rounds() == 10
     lib.dpd_version.restype = ctypes.c_char_p
     assert b"Philox-4x32-10" in lib.dpd_version()
+
