@@ -276,6 +276,49 @@ def run_batched(args, stream, world, rank):
             "stages_ms": {k: round(t, 5) for k, t in zip(dpd.STAGE_NAMES, stage_ms)}}
 
 
+def run_mixture(args, stream):
+    """Binary mixture (species with their own a, gamma and cut-off per pair) on
+    an L = 64 box against one species on the same box, same stencil."""
+    import numpy as np
+    import torch
+
+    import paper_1911_04712_gb300.dpd as dpd
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+    L, steps = args.mix_L, args.mix_steps
+    x, v = uniform_box_state(L, rho=3.0, seed=args.seed + 7)
+    n = len(x)
+    species = (np.arange(n) % 2).astype(np.int32)
+    a = np.array([[25.0, 40.0], [40.0, 25.0]])
+    g = np.array([[4.5, 4.5], [4.5, 4.5]])
+    rc = np.array([[1.0, 0.9], [0.9, 1.0]])
+    stencil = 1 if args.stencil == "half" else 0
+    out = {}
+    for name in ("mixture", "one_species"):
+        box = dpd.Box(L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=args.seed,
+                      stream=stream, stencil=stencil)
+        if name == "mixture":
+            box.set_species(a, g, rc)
+            box.set_state(x, v, species=species)
+        else:
+            box.set_state(x, v)
+        box.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        box.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"value": n * steps / (e0.elapsed_time(e1) / 1000.0), "ms_per_step": ms}
+        box.close()
+    return {"workload": f"binary mixture L={L:g} rho=3, 50/50, a = [[25, 40], [40, 25]], "
+                        "gamma 4.5, rc = [[1, 0.9], [0.9, 1]]",
+            "particles": n, "steps": steps, "stencil": args.stencil, "unit": UNIT,
+            "value": out["mixture"]["value"], "ms_per_step": out["mixture"]["ms_per_step"],
+            "one_species": out["one_species"],
+            "kernel": "general force kernel (per-pair species tables)"}
+
+
 def run_served(args, rank=0, world=1):
     """Prefix of the served request stream: Poisson arrivals submitted in real
     time to one continuous-batching queue per GPU under a 120 GB HBM budget
@@ -462,6 +505,10 @@ def run_native(args):
     if not args.no_served:
         served = run_served(args, rank, world)
 
+    mixture = None
+    if not args.no_mixture:
+        mixture = run_mixture(args, stream)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.cpu_L, rho, args.cpu_steps)
@@ -492,6 +539,7 @@ def run_native(args):
             "cpu_baseline": base,
             "batched": batched,
             "served": served,
+            "mixture": mixture,
         }
         print(json.dumps(out), flush=True)
     box.close()
@@ -521,6 +569,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-mixture", action="store_true")
+    ap.add_argument("--mix-L", type=float, default=64.0)
+    ap.add_argument("--mix-steps", type=int, default=200)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--nbox", type=int, default=512)

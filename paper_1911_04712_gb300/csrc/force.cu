@@ -820,8 +820,11 @@ static void launch_k(const Packed &P, int s0, int s1, bool fuse, cudaStream_t s)
 template <bool SINGLE, bool HALF>
 static void launch_variant(int v, bool gauss, const Packed &P, int s0, int s1, bool fuse,
                            cudaStream_t s) {
-  if (gauss) {  // one configuration serves bands that hold Gaussian-noise boxes
-    launch_k<SINGLE, HALF, 128, 24, false, true>(P, s0, s1, fuse, s);
+  if (gauss) {  // general kernels: bands holding Gaussian-noise or several-species boxes
+    if constexpr (HALF)
+      launch_k<SINGLE, HALF, 128, 24, false, true, true>(P, s0, s1, fuse, s);  // spread drain
+    else
+      launch_k<SINGLE, HALF, 128, 24, false, true>(P, s0, s1, fuse, s);
     return;
   }
   switch (v) {

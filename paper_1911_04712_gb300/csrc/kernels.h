@@ -43,7 +43,7 @@ struct TileGrid {
 // A contiguous slot range whose force kernel uses one variant.
 struct ForceBand {
   int slot0, slot1, variant;
-  int gauss;  // 1: some box of the band draws Gaussian noise
+  int gauss;  // 1: the band needs the general kernel (Gaussian noise or several species)
 };
 constexpr int kMaxBands = 8;
 constexpr int kNumForceVariants = 13;
