@@ -133,6 +133,7 @@ Engine::~Engine() {
     if (d_tiles_) cudaFree(d_tiles_);
     for (void *q : {(void *)d_wbeg_, (void *)d_from_, (void *)d_acc_, (void *)d_spart_})
       if (q) cudaFree(q);
+    if (h_sum_) cudaFreeHost(h_sum_);
     if (cap_) cudaStreamDestroy(cap_);
     if (cur >= 0 && cur != device_) cudaSetDevice(cur);
   }
@@ -307,10 +308,11 @@ int Engine::build_tiles() {
 }
 
 void Engine::drop_graph() {
-  if (graph_) {
-    cudaGraphExecDestroy(graph_);
-    graph_ = nullptr;
-  }
+  for (cudaGraphExec_t *g : {&graph_, &graph1_})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
 }
 
 int Engine::free_all() {
@@ -514,15 +516,18 @@ int Engine::rebuild() {
   return DPD_OK;
 }
 
-int Engine::capture_graph() {
-  drop_graph();
+int Engine::capture_graph(int nsteps, cudaGraphExec_t *out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
   const Packed P = packed();
   cudaGraph_t g = nullptr;
   DPD_CUDA_TRY(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   const bool fz = fused_steps();  // steps inside the chunk fused, the last one plain
-  for (int k = 0; k < graph_chunk && e == cudaSuccess; ++k) {
-    e = launch_step(P, true, true, cfg_, cap_, fz && k > 0, fz && k + 1 < graph_chunk);
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    e = launch_step(P, true, true, cfg_, cap_, fz && k > 0, fz && k + 1 < nsteps);
     if (e == cudaSuccess && sample_every_ > 0)
       e = launch_sample(P, d_.work, (int)work_.size(), d_wbeg_, d_from_, sample_every_, nbins_,
                         d_spart_, d_acc_, cap_);
@@ -534,10 +539,10 @@ int Engine::capture_graph() {
     return set_error(DPD_ERR_CUDA, "graph capture failed: %s",
                      cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(&graph_, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    graph_ = nullptr;
+    *out = nullptr;
     return set_error(DPD_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
   }
   return DPD_OK;
@@ -561,13 +566,21 @@ int Engine::step(int64_t nsteps) {
   int64_t left = nsteps;
   if (graph_chunk > 1 && left >= graph_chunk) {
     if (!graph_) {
-      int rc = capture_graph();
+      int rc = capture_graph(graph_chunk, &graph_);
       if (rc) return rc;
     }
     while (left >= graph_chunk) {
       DPD_CUDA_TRY(cudaGraphLaunch(graph_, stream_));
       left -= graph_chunk;
     }
+  }
+  if (left == 1 && graph_chunk > 1) {  // one step: a cached one-step graph, one launch
+    if (!graph1_) {
+      int rc = capture_graph(1, &graph1_);
+      if (rc) return rc;
+    }
+    DPD_CUDA_TRY(cudaGraphLaunch(graph1_, stream_));
+    left = 0;
   }
   const Packed P = packed();
   const bool fz = fused_steps();  // the last step of the call stays plain: read-outs follow
@@ -664,7 +677,7 @@ int Engine::gather(int box, float *pos, float *vel, float *frc, bool device_ptr)
 
 int Engine::build_work() {
   const int nb = nbox();
-  constexpr int kChunk = 32768;
+  constexpr int kChunk = 4096;  // particles per statistics block
   work_.clear();
   wbeg_.assign(nb + 1, 0);
   for (int b = 0; b < nb; ++b) {
@@ -677,12 +690,12 @@ int Engine::build_work() {
     for (int q = s0; q < s1; q += kChunk) work_.push_back(StatsWork{b, q, std::min(q + kChunk, s1), 0});
   }
   wbeg_[nb] = (int)work_.size();
-  if (work_.size() > d_.capW) {
+  if (work_.size() + nb > d_.capW) {  // partials of the work items, then per-box totals
     if (d_.work) cudaFree(d_.work);
     if (d_.part) cudaFree(d_.part);
     d_.work = nullptr;
     d_.part = nullptr;
-    const size_t cap = work_.size() * 2;
+    const size_t cap = (work_.size() + nb) * 2;
     DPD_CUDA_TRY(cudaMalloc(&d_.work, cap * sizeof(StatsWork)));
     DPD_CUDA_TRY(cudaMalloc(&d_.part, cap * kStatsFields * sizeof(double)));
     d_.capW = cap;
@@ -724,15 +737,22 @@ int Engine::box_sums(std::vector<double> &sums) {
     int rc = build_work();
     if (rc) return rc;
   }
-  std::vector<double> part(work_.size() * kStatsFields);
-  DPD_CUDA_TRY(launch_stats(packed(), d_.work, (int)work_.size(), d_.part, stream_));
-  DPD_CUDA_TRY(cudaMemcpyAsync(part.data(), d_.part, part.size() * sizeof(double),
-                               cudaMemcpyDeviceToHost, stream_));
+  // partial sums per work item, then per-box totals on the device (work
+  // order), behind the partials in the same buffer; one small copy to pinned memory
+  const size_t nsum = (size_t)nb * kStatsFields;
+  if (nsum > cap_hsum_) {
+    if (h_sum_) cudaFreeHost(h_sum_);
+    h_sum_ = nullptr;
+    DPD_CUDA_TRY(cudaMallocHost(&h_sum_, nsum * 2 * sizeof(double)));
+    cap_hsum_ = nsum * 2;
+  }
+  double *box_out = d_.part + work_.size() * kStatsFields;  // capacity: work items + boxes
+  DPD_CUDA_TRY(launch_stats(packed(), d_.work, (int)work_.size(), d_.part, stream_, d_wbeg_, nb,
+                            box_out));
+  DPD_CUDA_TRY(cudaMemcpyAsync(h_sum_, box_out, nsum * sizeof(double), cudaMemcpyDeviceToHost,
+                               stream_));
   DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
-  sums.assign((size_t)nb * kStatsFields, 0.0);
-  for (size_t w = 0; w < work_.size(); ++w)
-    for (int k = 0; k < kStatsFields; ++k)
-      sums[(size_t)work_[w].box * kStatsFields + k] += part[w * kStatsFields + k];
+  sums.assign(h_sum_, h_sum_ + nsum);
   return DPD_OK;
 }
 

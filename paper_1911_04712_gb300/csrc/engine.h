@@ -151,7 +151,7 @@ class Engine {
   Packed packed() const;
   int reserve(size_t np, size_t nc, size_t nb);
   int free_all();
-  int capture_graph();
+  int capture_graph(int nsteps, cudaGraphExec_t *out);
   void drop_graph();
 
   int device_ = -1;
@@ -177,6 +177,8 @@ class Engine {
   std::vector<StatsWork> work_;
   std::vector<int> wbeg_;            // first work item of each box (nbox + 1)
   int *d_wbeg_ = nullptr;
+  double *h_sum_ = nullptr;  // pinned per-box statistics totals
+  size_t cap_hsum_ = 0;
   size_t cap_wbeg_ = 0;
   bool work_dirty_ = true;
   int build_work();
@@ -187,7 +189,8 @@ class Engine {
   size_t cap_from_ = 0, cap_acc_ = 0, cap_spart_ = 0;
   int ensure_sampling_buffers();
   int launch_extra(const Packed &P, cudaStream_t s);
-  cudaGraphExec_t graph_ = nullptr;
+  cudaGraphExec_t graph_ = nullptr;   // graph_chunk steps
+  cudaGraphExec_t graph1_ = nullptr;  // one step (calls that end with a single step)
 };
 
 }  // namespace dpd

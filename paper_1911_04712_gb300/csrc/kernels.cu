@@ -228,20 +228,38 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(Packed P, const StatsWo
   const BoxDev B = P.boxes[w.box];
   const BoxState S = P.st[w.box];
   const float h = S.pending ? B.hdt_m : 0.0f;
-  double acc[kStatsFields] = {0, 0, 0, 0, 0, 0};
+  // Each thread sums its particles' FP32 values as unevaluated pairs
+  // hi + lo of FP32 numbers (the error-free TwoSum transformation: each
+  // addition's rounding error is carried in lo), about 2^-44 relative for
+  // these few terms, on the FP32 pipes; the pairs convert exactly to FP64
+  // and everything above the thread is summed in FP64.  (FP64 arithmetic
+  // per particle ran at a small fraction of the FP32 rate.)
+  float hi[kStatsFields - 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float lo[kStatsFields - 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  auto two_sum = [&](int k, float x) {
+    const float t = hi[k] + x;
+    const float xv = t - hi[k];
+    lo[k] += (hi[k] - (t - xv)) + (x - xv);
+    hi[k] = t;
+  };
+  int cnt = 0;
   for (int p = w.begin + threadIdx.x; p < w.end; p += kStatsThreads) {
     float4 v = P.vel[p];
     const float4 f = P.frc[p];
     v.x = fmaf(h, f.x, v.x);
     v.y = fmaf(h, f.y, v.y);
     v.z = fmaf(h, f.z, v.z);
-    acc[0] += (double)v.x;
-    acc[1] += (double)v.y;
-    acc[2] += (double)v.z;
-    acc[3] += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
-    acc[4] += (double)f.w;
-    acc[5] += 1.0;
+    two_sum(0, v.x);
+    two_sum(1, v.y);
+    two_sum(2, v.z);
+    two_sum(3, fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)));
+    two_sum(4, f.w);
+    ++cnt;
   }
+  double acc[kStatsFields];
+#pragma unroll
+  for (int k = 0; k < kStatsFields - 1; ++k) acc[k] = (double)hi[k] + (double)lo[k];
+  acc[kStatsFields - 1] = (double)cnt;
   __shared__ double red[kStatsFields][kStatsThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -558,10 +576,37 @@ cudaError_t launch_step_timed(const Packed &P, const StepConfig &cfg, cudaStream
   return cudaEventRecord(ev[5], s);
 }
 
+// Per-box totals of the work items' partial sums (work items of a box are
+// contiguous, wbeg[b] .. wbeg[b + 1]): one block per box, each thread a
+// strided sum, then a tree in a fixed order, so a box's totals do not
+// depend on the other boxes packed with it.
+constexpr int kBoxSumThreads = 128;
+__global__ void __launch_bounds__(kBoxSumThreads)
+    k_stats_boxes(const double *__restrict__ part, const int *__restrict__ wbeg,
+                  double *__restrict__ out) {
+  __shared__ double red[kStatsFields][kBoxSumThreads];
+  const int b = blockIdx.x, t = threadIdx.x;
+  double acc[kStatsFields] = {0, 0, 0, 0, 0, 0};
+  for (int w = wbeg[b] + t; w < wbeg[b + 1]; w += kBoxSumThreads)
+#pragma unroll
+    for (int k = 0; k < kStatsFields; ++k) acc[k] += part[(size_t)w * kStatsFields + k];
+#pragma unroll
+  for (int k = 0; k < kStatsFields; ++k) red[k][t] = acc[k];
+  __syncthreads();
+  for (int h = kBoxSumThreads / 2; h > 0; h >>= 1) {
+    if (t < h)
+#pragma unroll
+      for (int k = 0; k < kStatsFields; ++k) red[k][t] += red[k][t + h];
+    __syncthreads();
+  }
+  if (t < kStatsFields) out[(size_t)b * kStatsFields + t] = red[t][0];
+}
+
 cudaError_t launch_stats(const Packed &P, const StatsWork *work, int nwork, double *out,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int *wbeg, int nbox, double *box_out) {
   if (nwork <= 0) return cudaSuccess;
   k_stats<<<nwork, kStatsThreads, 0, s>>>(P, work, out);
+  if (box_out && nbox > 0) k_stats_boxes<<<nbox, kBoxSumThreads, 0, s>>>(out, wbeg, box_out);
   return cudaGetLastError();
 }
 

@@ -178,8 +178,10 @@ constexpr int kNumStages = 5;
 constexpr int kKernelsPerStep = 7;
 
 // Per-work-item FP64 partial sums for box statistics.
+// With box_out: also the per-box totals (nbox x kStatsFields, a fixed order per box).
 cudaError_t launch_stats(const Packed &P, const StatsWork *work, int nwork, double *out,
-                         cudaStream_t s);
+                         cudaStream_t s, const int *wbeg = nullptr, int nbox = 0,
+                         double *box_out = nullptr);
 
 // Write slots [slot0, slot0 + n) to id order as n x 3 arrays (any may be null);
 // velocities are full-step (pending half kick applied).

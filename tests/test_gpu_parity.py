@@ -267,6 +267,26 @@ def test_fused_integrate_gives_the_same_bits(dpd, body):
     assert s1["virial"] == s0["virial"] and s1["step"] == s0["step"] == 74
 
 
+def test_box_sums_match_fp64_sums_of_the_state(dpd):
+    """The statistics' box sums against FP64 sums of the same FP32 velocities
+    read back: momentum to 1e-10 of sum |v| (the per-thread sums are
+    error-free pairs of FP32 numbers, the rest FP64); the kinetic energy to
+    1e-7 (|v|^2 is formed in FP32)."""
+    L = 24.0
+    x, v = uniform_box_state(L, rho=3, seed=3)
+    p = _params(L, seed=3)
+    box = _box(dpd, p)
+    box.set_state(x, v)
+    box.step(7)
+    st = box.stats()
+    _, vg = box.get_state()
+    vd = vg.astype(np.float64)
+    P = vd.sum(0)
+    assert np.abs(np.asarray(st["momentum"]) - P).max() <= 1e-10 * np.abs(vd).sum()
+    ke = 0.5 * (vd ** 2).sum()
+    assert st["kinetic"] == pytest.approx(ke, rel=1e-7)
+
+
 def test_device_pointer_io_matches_host(dpd):
     import torch
     L = 6.0
