@@ -395,7 +395,7 @@ DPD_API int dpd_queue_get_stats(dpd_queue *q, dpd_queue_stats *out);
  * FP32 DEVICE output, in the same order.  The result equals what
  * dpd_set_state + dpd_get_forces gives for the same state at step 0.
  *
- * Allocates nothing: the scratch (about 3.3 MB) is one static device array
+ * Allocates nothing: the scratch (about 3.5 MB) is one static device array
  * of the library, held by every GPU that loads it until the process exits.
  * Limits: n <= DPD_NOALLOC_MAX_PARTICLES and at most DPD_NOALLOC_MAX_CELLS
  * cells (floor(L_d / rc) multiplied over the three axes); larger inputs

@@ -30,8 +30,15 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 constexpr int kSpeciesShift = 30;
 constexpr uint32_t kIdMask = (1u << kSpeciesShift) - 1u;
 constexpr int kMaxSpecies = 4;
-constexpr int kCellBits = 10;                 // packed cell coords: 10 bits per axis
+// Cells: floor(L_d / rc) per axis, each cut into kSlicesX slices along x
+// (the cell list's x resolution: a row is scanned only over the slices
+// within rc of the particle's x).
+constexpr int kSlicesX = 2;
+constexpr int kCellBits = 10;                 // packed cell coords: 10 bits for y and z,
+constexpr int kSliceBits = 12;                // 12 for the x slice
 constexpr int kMaxCellsPerAxis = (1 << kCellBits) - 1;
+static_assert(kSlicesX >= 2 && kSlicesX * kMaxCellsPerAxis < (1 << kSliceBits),
+              "an x window must not cover a slice twice; slices must fit the packed field");
 
 // Error bits raised by kernels into the context's device error word.
 constexpr unsigned kErrNonFinite = 1u;        // a position or velocity is NaN/Inf
@@ -41,8 +48,9 @@ constexpr unsigned kErrSpecies = 4u;          // a loaded species outside 0..nsp
 // Constants of one periodic box (read-only during a step).
 struct BoxDev {
   float L[3];       // box edges
-  float invh[3];    // cells per unit length, n_d / L_d
-  int n[3];         // cells per axis, floor(L_d / rc) >= 3
+  float invh[3];    // cells (x: slices) per unit length, n_d / L_d
+  int n[3];         // x: slices, kSlicesX floor(L_x / rc); y, z: cells, floor(L_d / rc) >= 3
+  float xwin;       // half-width of the x window: rc plus a margin of several ulp of L
   int cellBase;     // first packed cell index of this box
   int pbase;        // first particle slot of this box
   int np;           // particles in this box
@@ -172,13 +180,15 @@ __device__ __forceinline__ int cell_axis(float x, float invh, int n) {
 }
 
 __device__ __forceinline__ int pack_cell(int cx, int cy, int cz) {
-  return cx | (cy << kCellBits) | (cz << (2 * kCellBits));
+  return (int)((uint32_t)cx | ((uint32_t)cy << kSliceBits) |
+               ((uint32_t)cz << (kSliceBits + kCellBits)));
 }
 
 __device__ __forceinline__ void unpack_cell(int c, int &cx, int &cy, int &cz) {
-  cx = c & kMaxCellsPerAxis;
-  cy = (c >> kCellBits) & kMaxCellsPerAxis;
-  cz = (c >> (2 * kCellBits)) & kMaxCellsPerAxis;
+  const uint32_t u = (uint32_t)c;
+  cx = (int)(u & ((1u << kSliceBits) - 1u));
+  cy = (int)((u >> kSliceBits) & kMaxCellsPerAxis);
+  cz = (int)((u >> (kSliceBits + kCellBits)) & kMaxCellsPerAxis);
 }
 
 // Largest b with pbase[b] <= p (pbase has nbox + 1 entries, non-decreasing).

@@ -36,8 +36,8 @@ int check_params(const BoxParams &bp, int n[3]) {
     if (nd > kMaxCellsPerAxis)
       return set_error(DPD_ERR_ARG, "box edge %d spans %g cells; at most %d per axis", k, nd,
                        kMaxCellsPerAxis);
-    n[k] = (int)nd;
-    cells *= nd;
+    n[k] = (int)nd * (k == 0 ? kSlicesX : 1);
+    cells *= (double)n[k];
   }
   if (cells > (double)(1 << 30)) return set_error(DPD_ERR_ARG, "too many cells (%g)", cells);
   auto nonneg = [](double v) { return std::isfinite(v) && v >= 0.0; };
@@ -73,12 +73,15 @@ int check_params(const BoxParams &bp, int n[3]) {
 BoxDev make_box_dev(const BoxParams &bp, int cellBase, int pbase, int np) {
   BoxDev d{};
   int n[3];
+  double lmax = 0.0;
   for (int k = 0; k < 3; ++k) {
-    n[k] = (int)std::floor(bp.L[k] / bp.rc);
+    n[k] = (int)std::floor(bp.L[k] / bp.rc) * (k == 0 ? kSlicesX : 1);
     d.L[k] = (float)bp.L[k];
     d.n[k] = n[k];
     d.invh[k] = (float)((double)n[k] / bp.L[k]);
+    lmax = std::max(lmax, bp.L[k]);
   }
+  d.xwin = (float)(bp.rc + 16.0 * std::ldexp(std::max(lmax, bp.rc), -23));
   d.cellBase = cellBase;
   d.pbase = pbase;
   d.np = np;
@@ -263,20 +266,21 @@ int Engine::build_tiles() {
   int tc_single = 0;
   for (int b = 0; b < nb; ++b) {
     const BoxDev &B = boxes_[b];
+    const int ncx = B.n[0] / kSlicesX;  // tiles are runs of whole cells
     const double V = (double)B.L[0] * B.L[1] * B.L[2];
     const double rho = (double)B.np / V;
-    int tc = tile_tc_override_ > 0 ? std::min(tile_tc_override_, B.n[0]) : tile_cells_for(rho, B.n[0]);
-    const double h3 = V / ((double)B.n[0] * B.n[1] * B.n[2]);
+    int tc = tile_tc_override_ > 0 ? std::min(tile_tc_override_, ncx) : tile_cells_for(rho, ncx);
+    const double h3 = V / ((double)ncx * B.n[1] * B.n[2]);
     const int need = (int)std::ceil(9.0 * (tc + 2) * rho * h3 * 1.35) + 64;
     stage_need = std::max(stage_need, need);
     if (b == 0) tc_single = tc;
     if (nb > 1) {
-      const int tpr = (B.n[0] + tc - 1) / tc;
+      const int tpr = (ncx + tc - 1) / tc;
       for (int cz = 0; cz < B.n[2]; ++cz)
         for (int cy = 0; cy < B.n[1]; ++cy)
           for (int t = 0; t < tpr; ++t) {
             const int cx0 = t * tc;
-            const int nc = std::min(tc, B.n[0] - cx0);
+            const int nc = std::min(tc, ncx - cx0);
             tiles_h_.push_back(make_int4(b, cy, cz, cx0 | (nc << 16)));
           }
     }
@@ -288,7 +292,7 @@ int Engine::build_tiles() {
     const BoxDev &B = boxes_[0];
     cfg_.grid.list = nullptr;
     cfg_.grid.tc = tc_single;
-    cfg_.grid.tpr = (B.n[0] + tc_single - 1) / tc_single;
+    cfg_.grid.tpr = (B.n[0] / kSlicesX + tc_single - 1) / tc_single;
     cfg_.grid.ntiles = cfg_.grid.tpr * B.n[1] * B.n[2];
   } else {
     if (tiles_h_.size() > cap_tiles_) {

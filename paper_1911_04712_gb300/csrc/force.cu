@@ -116,7 +116,11 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   const uint32_t idi = __float_as_uint(pi.w);
   const uint32_t slo = (uint32_t)S.step, shi = (uint32_t)(S.step >> 32);
   const float Lx = B.L[0], Ly = B.L[1], Lz = B.L[2];
-  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];  // nx: x slices
+  // x window of every row: the slices xlo .. xhi hold every neighbour with
+  // |x_j - x_i| < rc (the margin makes it conservative)
+  const int xlo = __float2int_rd((pi.x - B.xwin) * B.invh[0]);
+  const int xhi = __float2int_rd((pi.x + B.xwin) * B.invh[0]);
   const uint32_t rc2m1 = __float_as_uint(B.rc2) - 1u;
   const bool k_is_one = (B.kexp == 1.0f);
   if constexpr (SPREAD) {
@@ -303,7 +307,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   };
 
   // Rows of the stencil.  Full: (dy, dz) in {-1,0,1}^2.  Half: the own row
-  // (own cell after p, then cell cx+1), row dy=+1 of the own plane, and the
+  // (forward from the slot after p), row dy=+1 of the own plane, and the
   // three rows of the plane dz=+1.
   constexpr int NROWS = HALF ? 5 : 9;
 #pragma unroll 1
@@ -338,65 +342,40 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       code |= kCodeIY;
     }
     const int rowbase = B.cellBase + (z * ny + y) * nx;
-    // Segments of this row: one contiguous slot range, or (across an x
-    // face) one range per cell with its own image shift.
+    // Slices xlo .. xhi of the row: one range of slots, or two across an x
+    // face, where the far part is the image r_j - L (xlo < 0) or is seen
+    // from r_i - L (xhi >= nx).  Half stencil, own row: forward from the
+    // slot after p (pairs within one slice belong to the lower slot).
     const bool own = HALF && r == 0;
-    const bool inner = own ? (cx + 1 <= nx - 1) : (cx >= 1 && cx <= nx - 2);
-    // Full stencil: a row across an x face is two ranges (two cells in place,
-    // one image cell).  Half stencil: one range per cell, which keeps its
-    // kernels (with the extra own-row case) below the spill point.
-    constexpr bool kMergeX = !HALF;
-    const int nseg = alive ? (inner ? 1 : ((own || kMergeX) ? 2 : 3)) : 0;
+    const int lo = own ? cx : xlo, hi = xhi;
+    const int nseg = alive ? ((lo < 0 || hi >= nx) ? 2 : 1) : 0;
     auto segment = [&](int sg, int &j0, int &j1, float &ax, float &jsx, uint32_t &c) {
       ax = pi.x;
       jsx = 0.f;
       c = code;
-      if (inner) {
-        j0 = own ? p + 1 : __ldg(P.start + rowbase + cx - 1);
-        j1 = __ldg(P.start + rowbase + cx + 2);
-      } else if (own) {  // cx == nx - 1: own cell after p, then cell 0 seen from r_i - L
+      if (lo < 0) {  // slices lo + nx .. nx - 1 as r_j - L, then 0 .. hi
         if (sg == 0) {
-          j0 = p + 1;
-          j1 = __ldg(P.start + rowbase + cx + 1);
-        } else {
-          j0 = __ldg(P.start + rowbase);
-          j1 = __ldg(P.start + rowbase + 1);
-          ax = pi.x - Lx;
-          c |= kCodeIX;
-        }
-      } else if (!kMergeX) {
-        int x = cx + sg - 1;
-        if (x < 0) {
-          x += nx;
-          jsx = Lx;
-          c |= kCodeJX;
-        } else if (x >= nx) {
-          x -= nx;
-          ax = pi.x - Lx;
-          c |= kCodeIX;
-        }
-        j0 = __ldg(P.start + rowbase + x);
-        j1 = __ldg(P.start + rowbase + x + 1);
-      } else if (cx == 0) {  // cells 0, 1 in place; cell nx-1 as the image r_j - L
-        if (sg == 0) {
-          j0 = __ldg(P.start + rowbase);
-          j1 = __ldg(P.start + rowbase + 2);
-        } else {
-          j0 = __ldg(P.start + rowbase + nx - 1);
+          j0 = __ldg(P.start + rowbase + lo + nx);
           j1 = __ldg(P.start + rowbase + nx);
           jsx = Lx;
           c |= kCodeJX;
+        } else {
+          j0 = __ldg(P.start + rowbase);
+          j1 = __ldg(P.start + rowbase + hi + 1);
         }
-      } else {  // cx == nx - 1: cells nx-2, nx-1 in place; cell 0 seen from r_i - L
+      } else if (hi >= nx) {  // lo .. nx - 1, then 0 .. hi - nx seen from r_i - L
         if (sg == 0) {
-          j0 = __ldg(P.start + rowbase + nx - 2);
+          j0 = own ? p + 1 : __ldg(P.start + rowbase + lo);
           j1 = __ldg(P.start + rowbase + nx);
         } else {
           j0 = __ldg(P.start + rowbase);
-          j1 = __ldg(P.start + rowbase + 1);
+          j1 = __ldg(P.start + rowbase + hi - nx + 1);
           ax = pi.x - Lx;
           c |= kCodeIX;
         }
+      } else {
+        j0 = own ? p + 1 : __ldg(P.start + rowbase + lo);
+        j1 = __ldg(P.start + rowbase + hi + 1);
       }
     };
     int sg = 0, j = 0, j1 = 0;
@@ -562,7 +541,7 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
     const int t = blockIdx.x;
     const int rowi = t / G.tpr;
     cx0 = (t - rowi * G.tpr) * G.tc;
-    nc = min(G.tc, B.n[0] - cx0);
+    nc = min(G.tc, B.n[0] / kSlicesX - cx0);
     cy = rowi % B.n[1];
     cz = rowi / B.n[1];
   } else {
@@ -576,7 +555,8 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
   }
   const BoxState S = P.st[b];
   if (!S.adv) return;  // uniform over the block
-  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  // the tile works in whole cells: cell x of a row is slices kSlicesX x .. kSlicesX x + kSlicesX - 1
+  const int nx = B.n[0] / kSlicesX, ny = B.n[1], nz = B.n[2];
   const float Lx = B.L[0], Ly = B.L[1], Lz = B.L[2];
   const int m0 = max(cx0 - 1, 0), m1 = min(cx0 + nc, nx - 1);
 
@@ -601,20 +581,20 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
       yy -= ny;
       R.ish |= kCodeIY;
     }
-    R.rb = B.cellBase + (zz * ny + yy) * nx;
-    R.gMain = __ldg(P.start + R.rb + m0);
-    R.lenMain = __ldg(P.start + R.rb + m1 + 1) - R.gMain;
+    R.rb = B.cellBase + (zz * ny + yy) * B.n[0];
+    R.gMain = __ldg(P.start + R.rb + kSlicesX * m0);
+    R.lenMain = __ldg(P.start + R.rb + kSlicesX * (m1 + 1)) - R.gMain;
     R.gBeg = 0;
     R.lenBeg = 0;
     if (cx0 == 0) {
-      R.gBeg = __ldg(P.start + R.rb + nx - 1);
-      R.lenBeg = __ldg(P.start + R.rb + nx) - R.gBeg;
+      R.gBeg = __ldg(P.start + R.rb + kSlicesX * (nx - 1));
+      R.lenBeg = __ldg(P.start + R.rb + kSlicesX * nx) - R.gBeg;
     }
     R.gEnd = 0;
     R.lenEnd = 0;
     if (cx0 + nc == nx) {
       R.gEnd = __ldg(P.start + R.rb);
-      R.lenEnd = __ldg(P.start + R.rb + 1) - R.gEnd;
+      R.lenEnd = __ldg(P.start + R.rb + kSlicesX) - R.gEnd;
     }
     R.off = 0;
     R.pad = 0;
@@ -637,8 +617,8 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
   uint32_t *lst = reinterpret_cast<uint32_t *>(tile_smem + 2 * G.stage_cap);
 
   // targets: the tile's own cells in the centre row (rows[4] is dy = dz = 0)
-  const int t0 = __ldg(P.start + rows[4].rb + cx0);
-  const int t1 = __ldg(P.start + rows[4].rb + cx0 + nc);
+  const int t0 = __ldg(P.start + rows[4].rb + kSlicesX * cx0);
+  const int t1 = __ldg(P.start + rows[4].rb + kSlicesX * (cx0 + nc));
 
   if (!staged) {
     // too many particles to stage: read neighbours from global memory
@@ -659,7 +639,7 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
     if (x < m0)
       v = R.off;
     else if (x <= m1 + 1)
-      v = R.off + R.lenBeg + (__ldg(P.start + R.rb + x) - R.gMain);
+      v = R.off + R.lenBeg + (__ldg(P.start + R.rb + kSlicesX * x) - R.gMain);
     else
       v = R.off + R.lenBeg + R.lenMain + R.lenEnd;
     sB[r][k] = v;
@@ -700,9 +680,9 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
       pi = __ldg(P.pos + p);
       vi = __ldg(P.vel + p);
     }
-    int cx, cyy, czz;
-    unpack_cell(__float_as_int(vi.w), cx, cyy, czz);
-    const int kt = cx - cx0 + 1;  // virtual cell of the target, 1..nc
+    int sx, cyy, czz;
+    unpack_cell(__float_as_int(vi.w), sx, cyy, czz);
+    const int kt = sx / kSlicesX - cx0 + 1;  // virtual cell of the target, 1..nc
     const uint32_t idi = __float_as_uint(pi.w);
     float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
     int cnt = 0;

@@ -35,7 +35,8 @@ namespace {
 
 constexpr int kNaMaxParticles = DPD_NOALLOC_MAX_PARTICLES;
 constexpr int kNaMaxCells = DPD_NOALLOC_MAX_CELLS;
-constexpr int kNaScanTiles = (kNaMaxCells + 1 + kScanTile - 1) / kScanTile;
+constexpr int kNaMaxSlices = kNaMaxCells * kSlicesX;  // entries of the cell list
+constexpr int kNaScanTiles = (kNaMaxSlices + 1 + kScanTile - 1) / kScanTile;
 constexpr size_t kNaCellCap = (size_t)kNaScanTiles * kScanTile;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -56,7 +57,7 @@ constexpr size_t kScratchBytes = kOffErr + align256(sizeof(unsigned));
 
 }  // namespace
 
-// The scratch: about 3.3 MB for 32768 particles and 32767 cells.
+// The scratch: about 3.5 MB for 32768 particles and 32767 cells (two x slices each).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Zero the cell counts and the error word; set the step of the force.
@@ -127,12 +128,12 @@ extern "C" int dpd_forces_noalloc(int64_t n, const float *pos, const float *vel,
   int nc[3];
   int rc_ = check_params(bp, nc);
   if (rc_) return rc_;
-  const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
-  if (ncell > kNaMaxCells)
+  const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];  // x slices of the cells
+  if (ncell > kNaMaxSlices)
     return set_error(DPD_ERR_ARG,
                      "dpd_forces_noalloc handles at most %d cells (box has %lld); use the "
                      "allocating context API for larger boxes",
-                     kNaMaxCells, (long long)ncell);
+                     kNaMaxCells, (long long)(ncell / kSlicesX));
   if (n == 0) return DPD_OK;
   if (!pos || !vel || !force) return set_error(DPD_ERR_ARG, "null device pointer");
 

@@ -51,7 +51,7 @@ struct Resident {
 size_t request_bytes(const BoxParams &bp, int64_t n) {
   int nc[3];
   for (int k = 0; k < 3; ++k) nc[k] = (int)std::floor(bp.L[k] / bp.rc);
-  const size_t cells = (size_t)nc[0] * nc[1] * nc[2];
+  const size_t cells = (size_t)nc[0] * nc[1] * nc[2] * dpd::kSlicesX;  // cell-list entries
   // particle arrays (5 float4 + 3 int32) and cell arrays (2 int32), plus slack
   return (size_t)n * (5 * 16 + 3 * 4) + cells * 2 * 4 + 4096;
 }
