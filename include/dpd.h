@@ -283,6 +283,11 @@ typedef struct {
     int flow_axis;       /* axis of the body force */
     int grad_axis;       /* axis on which the Poiseuille force switches sign */
     int noise;           /* DPD_NOISE_UNIFORM or DPD_NOISE_GAUSSIAN */
+    int nspecies;        /* 0 or 1: one species; 2..DPD_MAX_SPECIES: the tables below, as
+                            for dpd_set_species, entry (s, t) at [DPD_MAX_SPECIES s + t] */
+    double species_a[DPD_MAX_SPECIES * DPD_MAX_SPECIES];
+    double species_gamma[DPD_MAX_SPECIES * DPD_MAX_SPECIES];
+    double species_rc[DPD_MAX_SPECIES * DPD_MAX_SPECIES];
 } dpd_box_desc;
 
 /* Create a batch of nbox boxes and allocate its device memory.
@@ -301,6 +306,10 @@ DPD_API int dpd_batch_set_option(dpd_batch *b, int key, double value);
  * forces of loaded boxes are built at the next step or read. */
 DPD_API int dpd_batch_set_state(dpd_batch *b, int box, const float *pos, const float *vel,
                                 int where);
+/* dpd_batch_set_state with a species per particle (see
+ * dpd_set_state_species); the box's descriptor gives the tables. */
+DPD_API int dpd_batch_set_state_species(dpd_batch *b, int box, const float *pos, const float *vel,
+                                        const int32_t *species, int where);
 /* Advance every box by nsteps (a box with a step limit stops at it).
  * Errors: DPD_ERR_STATE while some box has not been loaded. */
 DPD_API int dpd_batch_step(dpd_batch *b, int64_t nsteps);

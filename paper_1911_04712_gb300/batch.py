@@ -24,7 +24,9 @@ class BoxDesc(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("n", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("kexp", ctypes.c_double), ("mass", ctypes.c_double),
                 ("body_force", ctypes.c_double), ("body_mode", ctypes.c_int),
-                ("flow_axis", ctypes.c_int), ("grad_axis", ctypes.c_int), ("noise", ctypes.c_int)]
+                ("flow_axis", ctypes.c_int), ("grad_axis", ctypes.c_int), ("noise", ctypes.c_int),
+                ("nspecies", ctypes.c_int), ("species_a", ctypes.c_double * 16),
+                ("species_gamma", ctypes.c_double * 16), ("species_rc", ctypes.c_double * 16)]
 
 
 def declare(L):
@@ -40,6 +42,7 @@ def declare(L):
     L.dpd_batch_set_stream.argtypes = [vp, vp]
     L.dpd_batch_set_option.argtypes = [vp, i32, dbl]
     L.dpd_batch_set_state.argtypes = [vp, i32, vp, vp, i32]
+    L.dpd_batch_set_state_species.argtypes = [vp, i32, vp, vp, vp, i32]
     L.dpd_batch_step.argtypes = [vp, i64]
     L.dpd_batch_get_state.argtypes = [vp, i32, vp, vp, i32]
     L.dpd_batch_get_forces.argtypes = [vp, i32, vp, i32]
@@ -48,7 +51,8 @@ def declare(L):
     L.dpd_batch_num_boxes.argtypes = [vp]
     for name in ("dpd_force_variant_info", "dpd_tuning_set", "dpd_tuning_get", "dpd_batch_create",
                  "dpd_batch_destroy", "dpd_batch_set_stream", "dpd_batch_set_option",
-                 "dpd_batch_set_state", "dpd_batch_step", "dpd_batch_get_state",
+                 "dpd_batch_set_state", "dpd_batch_set_state_species", "dpd_batch_step",
+                 "dpd_batch_get_state",
                  "dpd_batch_get_forces", "dpd_batch_get_stats", "dpd_batch_profile_steps",
                  "dpd_batch_num_boxes"):
         getattr(L, name).restype = i32
@@ -104,10 +108,18 @@ def tuning_get(table: int):
 
 def make_desc(L, n, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=0, steps=0, kexp=1.0,
               mass=1.0, body_force=0.0, body_mode=0, flow_axis=2, grad_axis=0,
-              noise=0) -> BoxDesc:
+              noise=0, species=None) -> BoxDesc:
+    """species: None, or (a, gamma, rc) S x S tables of several species."""
     L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+    nsp, tabs = 1, [[0.0] * 16 for _ in range(3)]
+    if species is not None:
+        t = [np.asarray(x, dtype=np.float64) for x in species]
+        nsp = t[0].shape[0]
+        tabs = [[float(x[s, u]) if s < nsp and u < nsp else 0.0 for s in range(4)
+                 for u in range(4)] for x in t]
     return BoxDesc((ctypes.c_double * 3)(*L3), a, gamma, kT, rc, dt, int(seed), int(n),
-                   int(steps), kexp, mass, body_force, body_mode, flow_axis, grad_axis, noise)
+                   int(steps), kexp, mass, body_force, body_mode, flow_axis, grad_axis, noise,
+                   nsp, *[(ctypes.c_double * 16)(*x) for x in tabs])
 
 
 class Batch:
@@ -144,13 +156,23 @@ class Batch:
     def set_option(self, key: int, value):
         _check(_lib().dpd_batch_set_option(self._b, int(key), float(value)))
 
-    def set_state(self, box: int, pos, vel):
-        from .dpd import _vec3_arg
+    def set_state(self, box: int, pos, vel, species=None):
+        """Load box `box`; species: one int per particle (host, same memory as pos), or None."""
+        from .dpd import WHERE_HOST, _vec3_arg
         pp, wp, kp = _vec3_arg(pos, self.n[box])
         vv, wv, kv = _vec3_arg(vel, self.n[box])
         if wp != wv:
             raise ValueError("pos and vel must both be host arrays or both CUDA tensors")
-        _check(_lib().dpd_batch_set_state(self._b, box, pp, vv, wp))
+        if species is None:
+            _check(_lib().dpd_batch_set_state(self._b, box, pp, vv, wp))
+        else:
+            if wp != WHERE_HOST:
+                raise ValueError("species with host positions and velocities")
+            sp = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
+            if sp.size != self.n[box]:
+                raise ValueError("species must have one entry per particle")
+            _check(_lib().dpd_batch_set_state_species(self._b, box, pp, vv,
+                                                      sp.ctypes.data_as(ctypes.c_void_p), wp))
 
     def step(self, nsteps: int = 1):
         _check(_lib().dpd_batch_step(self._b, int(nsteps)))

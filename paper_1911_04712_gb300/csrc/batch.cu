@@ -102,6 +102,13 @@ int dpd_batch_create(dpd_batch **out, int nbox, const dpd_box_desc *descs) {
     bp.fb_grad = d.grad_axis;
     bp.seed = d.seed;
     bp.noise = d.noise;
+    bp.nspec = d.nspecies <= 1 ? 1 : d.nspecies;
+    if (bp.nspec > 1)
+      for (int k = 0; k < DPD_MAX_SPECIES * DPD_MAX_SPECIES; ++k) {
+        bp.sa[k] = d.species_a[k];
+        bp.sg[k] = d.species_gamma[k];
+        bp.src[k] = d.species_rc[k];
+      }
     int nc[3];
     int rc = dpd::check_params(bp, nc);
     if (rc) return dpd::set_error(rc, "box %d: %s", i, dpd_last_error());
@@ -180,6 +187,9 @@ int dpd_batch_set_option(dpd_batch *b, int key, double value) {
       if ((rc = as_int(0, 1 << 20, &v))) return rc;
       int t = b->tiles, c = b->tile_cells, cap = b->stage_cap;
       if (key == DPD_PARAM_FORCE_TILES) t = v != 0;
+      for (const BoxParams &bp : b->params)
+        if (t && bp.nspec > 1)
+          return dpd::set_error(DPD_ERR_ARG, "the staged force tiles serve one species only");
       if (key == DPD_PARAM_TILE_CELLS) c = v;
       if (key == DPD_PARAM_STAGE_CAP) cap = v;
       if ((rc = b->eng.set_tiling(t, c, cap))) return rc;
@@ -196,16 +206,24 @@ int dpd_batch_set_option(dpd_batch *b, int key, double value) {
   }
 }
 
-int dpd_batch_set_state(dpd_batch *b, int box, const float *pos, const float *vel, int where) {
+int dpd_batch_set_state_species(dpd_batch *b, int box, const float *pos, const float *vel,
+                                const int32_t *species, int where) {
   dpd::clear_error();
   if (!b) return dpd::set_error(DPD_ERR_ARG, "null batch");
   int rc = box_index(b, box);
   if (rc) return rc;
   if (where != DPD_WHERE_HOST && where != DPD_WHERE_DEVICE)
     return dpd::set_error(DPD_ERR_ARG, "bad where");
+  const int nspec = b->params[box].nspec;
+  if (species && where == DPD_WHERE_HOST)
+    for (int64_t i = 0; i < b->n[box]; ++i)
+      if (species[i] < 0 || species[i] >= nspec)
+        return dpd::set_error(DPD_ERR_ARG, "box %d, particle %lld: species %d outside 0..%d", box,
+                              (long long)i, species[i], nspec - 1);
   const int k = b->slot[box];
-  rc = b->eng.load_box(k, pos, vel, where == DPD_WHERE_DEVICE);
+  rc = b->eng.load_box(k, pos, vel, where == DPD_WHERE_DEVICE, species);
   if (rc) return rc;
+  if (species && where == DPD_WHERE_DEVICE && (rc = b->eng.check_error())) return rc;
   b->eng.set_box_state(k, 0, b->steps[box]);
   if (!b->loaded[box]) {
     b->loaded[box] = 1;
@@ -213,6 +231,10 @@ int dpd_batch_set_state(dpd_batch *b, int box, const float *pos, const float *ve
   }
   b->dirty = true;
   return DPD_OK;
+}
+
+int dpd_batch_set_state(dpd_batch *b, int box, const float *pos, const float *vel, int where) {
+  return dpd_batch_set_state_species(b, box, pos, vel, nullptr, where);
 }
 
 int dpd_batch_step(dpd_batch *b, int64_t nsteps) {

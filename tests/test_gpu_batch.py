@@ -156,6 +156,45 @@ def test_batch_fused_integrate_with_step_limits(mods):
         assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
 
 
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_batch_with_species_equals_each_box_alone(mods, stencil):
+    """Boxes of several species packed with one-species boxes (the general
+    force kernel's bands beside the tuned ones): each box as alone in a
+    context with the same tables (bitwise for the full stencil)."""
+    D, B = mods
+    specs, states = _mix(6, seed=9)
+    A = np.array([[25.0, 40.0, 31.0], [40.0, 18.0, 55.0], [31.0, 55.0, 12.0]])
+    G = np.array([[4.5, 2.0, 6.0], [2.0, 3.5, 1.5], [6.0, 1.5, 8.0]])
+    R = np.array([[1.0, 0.8, 0.9], [0.8, 0.7, 0.95], [0.9, 0.95, 0.85]])
+    tables = [None, (A, G, R), None, (A[:2, :2], G[:2, :2], R[:2, :2]), (A, G, R), None]
+    labels = [None if t is None else
+              np.random.default_rng(k).integers(0, t[0].shape[0], len(st[0])).astype(np.int32)
+              for k, (t, st) in enumerate(zip(tables, states))]
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed,
+                         species=t) for s, st, t in zip(specs, states, tables)]
+    bt = B.Batch(descs, stencil=stencil)
+    for k, (x, v) in enumerate(states):
+        bt.set_state(k, x, v, species=labels[k])
+    bt.step(40)
+    for k, (s, (x, v)) in enumerate(zip(specs, states)):
+        box = D.Box(s.L, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed,
+                    stencil=stencil)
+        if tables[k] is not None:
+            box.set_species(*tables[k])
+        box.set_state(x, v, species=labels[k])
+        box.step(40)
+        xa, fa = box.get_state()[0], box.get_forces()
+        xb, fb = bt.get_state(k)[0], bt.get_forces(k)
+        if stencil == 0:
+            assert np.array_equal(xa, xb) and np.array_equal(fa, fb), k
+        else:
+            d = xb.astype(np.float64) - xa
+            d -= s.L * np.round(d / s.L)
+            assert np.abs(d).max() < 1e-4, k
+        box.close()
+    bt.close()
+
+
 def test_batch_boxes_match_oracle(mods):
     D, B = mods
     specs, states = _mix(6, seed=4)
