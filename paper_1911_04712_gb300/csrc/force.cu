@@ -1,7 +1,12 @@
 // Force kernels of the DPD step: pair forces (Sec. 2.1, Eqs. 2-5) over the
-// cell list (Sec. 3.2), in variants that differ in block size and pair-list
-// capacity (chosen per density band from a tuning table), plus the optional
-// shared-memory staged tiles.
+// cell list (Sec. 3.2).  One thread per target particle collects its
+// neighbours inside rc into a shared-memory pair list and then evaluates
+// them; the variants differ in block size, list capacity and how a warp
+// drains its lists (per lane, balanced in list order, or spread over the
+// lanes with atomic sums), chosen per density band from tuning tables.
+// General variants also serve Gaussian noise and several species.  The full
+// stencil can fuse the next step's integrate into its epilogue.  Plus the
+// optional shared-memory staged tiles.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,12 +83,6 @@ __device__ __forceinline__ int scan_range(const float4 *__restrict__ pos, int j0
   return -1;
 }
 
-// Force on one target particle in slot p from the 27-cell (full) or 13-cell
-// + own-cell (half) neighbourhood, reading neighbours from global memory.
-// Every lane of the warp must call this (dead lanes with alive = false):
-// the rows are walked in a warp-uniform loop and the lists are drained at a
-// single warp-uniform point, when a list is nearly full or after a row once
-// any lane holds more than CAP/2 entries.
 // Per-warp scratch of the balanced drain.  List of lane l: list[l * (CAP+1) + k].
 template <int CAP>
 struct WarpScratch {
@@ -93,6 +92,14 @@ struct WarpScratch {
   float4 res[32];       // pair results of the chunk being processed
   int start[32];        // lane whose list starts at this chunk position, or -1
 };
+
+// Force on one target particle in slot p from the 27-cell (full) or 13-cell
+// + own-cell (half) neighbourhood, each row scanned over the x slices within
+// rc of the particle, reading neighbours from global memory.  Every lane of
+// the warp must call this (dead lanes with alive = false): the rows are
+// walked in a warp-uniform loop and the lists are drained at a single
+// warp-uniform point, when a list is nearly full or after a row once any
+// lane holds more than CAP/2 entries.
 
 template <bool HALF, int NT, int CAP, bool BAL = false, bool GAUSS = false, bool SPREAD = false>
 __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, const BoxState &S,

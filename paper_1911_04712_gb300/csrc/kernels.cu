@@ -3,17 +3,21 @@
 // One step, every stage a kernel over the packed particle slots (the force
 // kernels are in force.cu):
 //   1. integrate_bin  kick (completing the previous step), kick, drift, wrap
-//                     (Sec. 3.1 item 5, Eq. 1); cell of the new position and
-//                     its arrival rank by an atomic count (Sec. 3.2);
+//                     (Sec. 3.1 item 5, Eq. 1); cell (x slice) of the new
+//                     position and its arrival rank by an atomic count
+//                     (Sec. 3.2); with the full stencil the previous step's
+//                     force kernel can do this instead (fused);
 //   2. scan           exclusive scan of the cell counts into cell starts
 //                     (three passes: tile sums, scan of the tile sums, apply);
-//   3. bin_keys       record each slot's old index at its arrival position;
-//   4. bin_scatter    rank by old index inside the cell (a stable counting
-//                     sort) and move position and velocity to the new slot;
+//   3. bin_keys       full stencil: record each slot's old index at its
+//                     arrival position;
+//   4. bin_scatter    move position and velocity to the new slot: full
+//                     stencil ranked by old index inside the cell (a stable
+//                     counting sort), half stencil by arrival rank;
 //   5. force          pair forces of Eqs. 2-5 over the 27 neighbouring cells
 //                     (full stencil) or 13 cells + own cell with Newton's third
 //                     law (half stencil, Sec. 3.2), plus the body force.
-// All arithmetic is FP32; statistics reduce in FP64.
+// All arithmetic is FP32; statistics sum in FP64 above each thread.
 #include <cuda_runtime.h>
 
 #include <cstdint>
