@@ -134,6 +134,7 @@ Engine::~Engine() {
     free_all();
     if (d_.err) cudaFree(d_.err);
     if (d_tiles_) cudaFree(d_tiles_);
+    if (d_mixed_) cudaFree(d_mixed_);
     for (void *q : {(void *)d_wbeg_, (void *)d_from_, (void *)d_acc_, (void *)d_spart_})
       if (q) cudaFree(q);
     if (h_sum_) cudaFreeHost(h_sum_);
@@ -233,6 +234,31 @@ int Engine::build_bands() {
     const int best = (int)(std::max_element(cover.begin(), cover.end()) - cover.begin());
     runs.assign(1, ForceBand{0, ntot_, best, anyg});
   }
+  // Packed sets: the warps of each band whose slots span two boxes (the
+  // device tests the same: the box of the first and of the last slot, the
+  // slots clamped to the packed set).  Warp-cooperative kernels skip them.
+  std::vector<int> mixed;
+  auto box_of_slot = [&](int p) {
+    return (int)(std::upper_bound(pbase_.begin(), pbase_.end(), p) - pbase_.begin()) - 1;
+  };
+  for (auto &r : runs) {
+    r.mw_off = (int)mixed.size();
+    if (nb > 1)
+      for (int p0 = r.slot0; p0 < r.slot1; p0 += 32)
+        if (box_of_slot(p0) != box_of_slot(std::min(p0 + 31, ntot_ - 1))) mixed.push_back(p0);
+    r.mw_count = (int)mixed.size() - r.mw_off;
+  }
+  if (mixed.size() > cap_mixed_) {
+    if (d_mixed_) cudaFree(d_mixed_);
+    d_mixed_ = nullptr;
+    cap_mixed_ = 0;
+    DPD_CUDA_TRY(cudaMalloc(&d_mixed_, mixed.size() * 2 * sizeof(int)));
+    cap_mixed_ = mixed.size() * 2;
+  }
+  if (!mixed.empty())
+    DPD_CUDA_TRY(cudaMemcpyAsync(d_mixed_, mixed.data(), mixed.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, stream_));
+  cfg_.mixed_warps = d_mixed_;
   cfg_.nbands = (int)runs.size();
   for (int k = 0; k < cfg_.nbands; ++k) cfg_.band[k] = runs[k];
   return DPD_OK;

@@ -162,6 +162,8 @@ class Engine {
   int stage_cap_override_ = 0;    // staging capacity forced by set_tiling (0: by density)
   std::vector<int4> tiles_h_;
   int4 *d_tiles_ = nullptr;
+  int *d_mixed_ = nullptr;        // first slots of the bands' two-box warps
+  size_t cap_mixed_ = 0;
   size_t cap_tiles_ = 0;
   int build_tiles();
   int build_bands();

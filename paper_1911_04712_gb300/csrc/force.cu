@@ -462,12 +462,13 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1, bo
   alive = alive && S.adv;
   // Lanes of this warp in more than one box.  Every lane counts, dead ones
   // too: past the end of a band they belong to the next band's box, and the
-  // balanced and spread drains hand them other lanes' entries.
-  bool mixed = false;
+  // balanced and spread drains hand them other lanes' entries.  Such warps
+  // are left to k_force_warps (the host lists them per band).
   if constexpr (!SINGLE && (BAL || SPREAD)) {
     const int b0 = __shfl_sync(0xffffffffu, b, 0);
-    mixed = !__all_sync(0xffffffffu, b == b0);
+    if (!__all_sync(0xffffffffu, b == b0)) return;
   }
+  constexpr bool mixed = false;
   auto run = [&](const BoxDev &B) {
     if constexpr (BAL) {
       WarpScratch<CAP> *W = &smem_warp[threadIdx.x >> 5];
@@ -488,6 +489,22 @@ __global__ void __launch_bounds__(NT) k_force(Packed P, int slot0, int slot1, bo
   } else {
     run(P.boxes[b]);  // read where used from the box table, not copied into registers
   }
+}
+
+// The warps of a packed set whose slots span two boxes, one block of 32
+// threads each (first slots in warp_start), with the per-lane drain: each
+// lane evaluates only its own pairs, with its own box's parameters.
+template <bool HALF, int CAP, bool GAUSS>
+__global__ void __launch_bounds__(32)
+    k_force_warps(Packed P, const int *__restrict__ warp_start, int slot1, bool fuse) {
+  __shared__ uint32_t smem_list[CAP * 32];
+  const int p = warp_start[blockIdx.x] + (int)threadIdx.x;
+  const bool real = p < slot1;
+  const int b = find_box(P.pbase, P.nbox, min(p, P.ntot - 1));
+  const BoxState S = P.st[b];
+  const bool alive = real && S.adv;
+  force_direct<HALF, 32, CAP, false, GAUSS>(P, P.boxes[b], S, p, alive, smem_list + threadIdx.x,
+                                            nullptr, nullptr, false, fuse, real);
 }
 
 // ------------------------------------------------------- staged force tiles
@@ -874,6 +891,19 @@ cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s,
         launch_variant<false, true>(b.variant, b.gauss, P, b.slot0, b.slot1, false, s);
       else
         launch_variant<false, false>(b.variant, b.gauss, P, b.slot0, b.slot1, fuse, s);
+      // the band's two-box warps, skipped by the warp-cooperative kernels
+      if (cfg.nbands > 0 && b.mw_count > 0 && cfg.mixed_warps &&
+          cooperative_variant(b.variant, b.gauss != 0, half)) {
+        const int *ws = cfg.mixed_warps + b.mw_off;
+        if (half) {
+          if (b.gauss)
+            k_force_warps<true, 24, true><<<b.mw_count, 32, 0, s>>>(P, ws, b.slot1, false);
+          else
+            k_force_warps<true, 24, false><<<b.mw_count, 32, 0, s>>>(P, ws, b.slot1, false);
+        } else {
+          k_force_warps<false, 24, false><<<b.mw_count, 32, 0, s>>>(P, ws, b.slot1, fuse);
+        }
+      }
     }
   }
   return cudaGetLastError();

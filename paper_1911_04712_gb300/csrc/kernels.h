@@ -44,6 +44,10 @@ struct TileGrid {
 struct ForceBand {
   int slot0, slot1, variant;
   int gauss;  // 1: the band needs the general kernel (Gaussian noise or several species)
+  // packed sets: the band's warps whose slots span two boxes (first slots at
+  // StepConfig::mixed_warps[mw_off ..]); warp-cooperative variants skip them
+  // and a second launch runs them with the per-lane drain
+  int mw_off, mw_count;
 };
 constexpr int kMaxBands = 8;
 constexpr int kNumForceVariants = 13;
@@ -55,7 +59,14 @@ struct StepConfig {
   TileGrid grid{};
   int nbands = 0;        // 0: one band over every slot with variant 0
   ForceBand band[kMaxBands]{};
+  const int *mixed_warps = nullptr;  // device: first slots of the bands' two-box warps
 };
+// Whether the variant drains over the whole warp (balanced or spread): such
+// kernels evaluate other lanes' entries with their own box's parameters.
+inline bool cooperative_variant(int v, bool general, bool half) {
+  if (general) return half;  // the half stencil's general kernel drains spread
+  return (v >= 7 && v <= 9) || (half && v >= 10 && v <= 12);
+}
 size_t tile_smem_bytes(int stage_cap);
 // fuse: full stencil only; the kernel also performs the next step's row a1
 // (integrate_one) for every slot and stores no force.
