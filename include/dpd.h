@@ -14,8 +14,11 @@
  *     (seed lo, seed hi), mapped to xi = sqrt(3)(2U - 1),
  *     U = ((u >> 8) + 1/2) 2^-24 (zero mean, unit variance);
  *   - cell lists rebuilt every step (Sec. 3.2): counting sort of particles
- *     into cells of edge h_d = L_d / floor(L_d / rc) >= rc, exclusive scan,
- *     stable reorder; forces summed over the 27 neighbouring cells;
+ *     into cells of edge h_d = L_d / floor(L_d / rc) >= rc (each cut into 2
+ *     slices along x), exclusive scan, reorder (stable by previous slot for
+ *     the full stencil, by arrival for the half stencil); forces summed over
+ *     the 27 neighbouring cells, or 13 of them plus the own cell with
+ *     Newton's third law (half stencil);
  *   - velocity-Verlet with the velocity predicted at the half step (the fused
  *     leapfrog of Sec. 3.1, item 5): v += dt/2 F/m; x += dt v (wrapped into
  *     [0, L)); F = F(x, v); v += dt/2 F/m.
@@ -23,7 +26,8 @@
  * Step index of the noise: the force computed by dpd_set_state uses step 0;
  * the force computed during the k-th call-counted step uses step k.
  *
- * Arithmetic: FP32 state and forces; FP64 for box-level reductions.
+ * Arithmetic: FP32 state and forces; box-level reductions sum in FP64 (each
+ * GPU thread's few terms as an error-free pair of FP32 numbers).
  *
  * Conventions for every call:
  *   - returns DPD_OK (0) or a negative DPD_ERR_* status; never aborts or
