@@ -220,33 +220,42 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(Packed P, bool zero
 // ------------------------------------------------------------------ stats
 constexpr int kStatsThreads = 256;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
+// Sum of two unevaluated pairs hi + lo of FP32 numbers, as such a pair: the
+// high parts are added error-free (TwoSum), the low parts and that error go
+// into the new low part, then the pair is renormalised (Dekker's Fast2Sum).
+// The result carries about 2^-44 of the operands' magnitude as error.
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bv = s - hi;
+  float e = (hi - (s - bv)) + (bh - bv);
+  e += lo + bl;
+  hi = s + e;
+  lo = e - (hi - s);
 }
 
 __global__ void __launch_bounds__(kStatsThreads) k_stats(Packed P, const StatsWork *__restrict__ work,
                                                          double *__restrict__ out) {
   const StatsWork w = work[blockIdx.x];
-  const BoxDev B = P.boxes[w.box];
+  const BoxDev &B = P.boxes[w.box];
   const BoxState S = P.st[w.box];
   const float h = S.pending ? B.hdt_m : 0.0f;
   // Each thread sums its particles' FP32 values as unevaluated pairs
   // hi + lo of FP32 numbers (the error-free TwoSum transformation: each
-  // addition's rounding error is carried in lo), about 2^-44 relative for
-  // these few terms, on the FP32 pipes; the pairs convert exactly to FP64
-  // and everything above the thread is summed in FP64.  (FP64 arithmetic
-  // per particle ran at a small fraction of the FP32 rate.)
-  float hi[kStatsFields - 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float lo[kStatsFields - 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  // addition's rounding error is carried in lo).  The warp and the block
+  // combine those pairs as pairs, and only the block's total is converted
+  // to FP64: every FP64 operation per particle or per lane is avoided,
+  // since FP64 runs at a small fraction of the FP32 rate on this part.
+  // Everything above the block (work items, boxes) is summed in FP64.
+  constexpr int F = kStatsFields - 1;
+  float hi[F] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float lo[F] = {0.f, 0.f, 0.f, 0.f, 0.f};
   auto two_sum = [&](int k, float x) {
     const float t = hi[k] + x;
     const float xv = t - hi[k];
     lo[k] += (hi[k] - (t - xv)) + (x - xv);
     hi[k] = t;
   };
-  int cnt = 0;
+#pragma unroll 4
   for (int p = w.begin + threadIdx.x; p < w.end; p += kStatsThreads) {
     float4 v = P.vel[p];
     const float4 f = P.frc[p];
@@ -258,24 +267,32 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(Packed P, const StatsWo
     two_sum(2, v.z);
     two_sum(3, fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)));
     two_sum(4, f.w);
-    ++cnt;
   }
-  double acc[kStatsFields];
 #pragma unroll
-  for (int k = 0; k < kStatsFields - 1; ++k) acc[k] = (double)hi[k] + (double)lo[k];
-  acc[kStatsFields - 1] = (double)cnt;
-  __shared__ double red[kStatsFields][kStatsThreads / 32];
+  for (int k = 0; k < F; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      pair_add(hi[k], lo[k], __shfl_down_sync(0xffffffffu, hi[k], o),
+               __shfl_down_sync(0xffffffffu, lo[k], o));
+  constexpr int NW = kStatsThreads / 32;
+  static_assert(NW <= 32 && (NW & (NW - 1)) == 0, "block of 1 to 32 warps, a power of two");
+  __shared__ float2 red[F][NW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
 #pragma unroll
-  for (int k = 0; k < kStatsFields; ++k) {
-    const double s = warp_sum_d(acc[k]);
-    if (lane == 0) red[k][warp] = s;
-  }
+    for (int k = 0; k < F; ++k) red[k][warp] = make_float2(hi[k], lo[k]);
   __syncthreads();
-  if (threadIdx.x < kStatsFields) {
-    double s = 0.0;
-    for (int q = 0; q < kStatsThreads / 32; ++q) s += red[threadIdx.x][q];
-    out[(size_t)blockIdx.x * kStatsFields + threadIdx.x] = s;
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+      float2 r = (lane < NW) ? red[k][lane] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = NW / 2; o > 0; o >>= 1)
+        pair_add(r.x, r.y, __shfl_down_sync(0xffffffffu, r.x, o),
+                 __shfl_down_sync(0xffffffffu, r.y, o));
+      if (lane == 0) out[(size_t)blockIdx.x * kStatsFields + k] = (double)r.x + (double)r.y;
+    }
+    if (lane == 0) out[(size_t)blockIdx.x * kStatsFields + F] = (double)(w.end - w.begin);
   }
 }
 
@@ -584,13 +601,14 @@ cudaError_t launch_step_timed(const Packed &P, const StepConfig &cfg, cudaStream
 // contiguous, wbeg[b] .. wbeg[b + 1]): one block per box, each thread a
 // strided sum, then a tree in a fixed order, so a box's totals do not
 // depend on the other boxes packed with it.
-constexpr int kBoxSumThreads = 128;
+constexpr int kBoxSumThreads = 512;
 __global__ void __launch_bounds__(kBoxSumThreads)
     k_stats_boxes(const double *__restrict__ part, const int *__restrict__ wbeg,
                   double *__restrict__ out) {
   __shared__ double red[kStatsFields][kBoxSumThreads];
   const int b = blockIdx.x, t = threadIdx.x;
   double acc[kStatsFields] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
   for (int w = wbeg[b] + t; w < wbeg[b + 1]; w += kBoxSumThreads)
 #pragma unroll
     for (int k = 0; k < kStatsFields; ++k) acc[k] += part[(size_t)w * kStatsFields + k];
