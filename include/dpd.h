@@ -66,6 +66,7 @@ extern "C" {
 #define DPD_ERR_NUMERIC (-5)  /* device flagged a non-finite position or force      */
 #define DPD_ERR_TIMEOUT (-6)  /* a bounded wait expired                              */
 #define DPD_ERR_BUSY (-7)     /* resource in use (e.g. result not ready)            */
+#define DPD_ERR_INTERNAL (-8) /* checked build only: a kernel's index check failed  */
 
 #define DPD_WHERE_HOST 0
 #define DPD_WHERE_DEVICE 1

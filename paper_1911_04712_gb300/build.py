@@ -16,11 +16,16 @@ LIB = os.path.join(HERE, "libdpd.so")
 PHILOX_ROUNDS = 10  # the noise generator's round count (Philox-4x32-10)
 
 
-def lib_path(philox_rounds: int = PHILOX_ROUNDS) -> str:
-    """The library file; other round counts (for a round-count study) build beside it."""
-    if philox_rounds == PHILOX_ROUNDS:
-        return LIB
-    return os.path.join(HERE, f"libdpd_r{philox_rounds}.so")
+def lib_path(philox_rounds: int = PHILOX_ROUNDS, checked: bool = False) -> str:
+    """The library file.  Other round counts (for a round-count study) and the
+    checked build (kernels test their derived indices, see DPD_IN_BOUNDS)
+    build beside it."""
+    name = "libdpd"
+    if philox_rounds != PHILOX_ROUNDS:
+        name += f"_r{philox_rounds}"
+    if checked:
+        name += "_checked"
+    return os.path.join(HERE, name + ".so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -49,17 +54,21 @@ def _stale(out: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
-          philox_rounds: int = PHILOX_ROUNDS) -> str:
+          philox_rounds: int = PHILOX_ROUNDS, checked: bool = False) -> str:
     nvcc = _nvcc()
     if not 1 <= philox_rounds <= 16:
         raise ValueError("Philox round count must be 1..16")
-    lib = lib_path(philox_rounds)
+    lib = lib_path(philox_rounds, checked)
     bdir = BUILD if philox_rounds == PHILOX_ROUNDS else BUILD + f"_r{philox_rounds}"
+    if checked:
+        bdir += "_checked"
     os.makedirs(bdir, exist_ok=True)
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if philox_rounds != PHILOX_ROUNDS:
         flags += [f"-DDPD_PHILOX_ROUNDS={philox_rounds}"]
+    if checked:
+        flags += ["-DDPD_CHECKED=1"]
     if extra:
         flags += extra
     if verbose:
@@ -96,4 +105,5 @@ if __name__ == "__main__":
     rounds = PHILOX_ROUNDS
     if "--philox-rounds" in sys.argv:
         rounds = int(sys.argv[sys.argv.index("--philox-rounds") + 1])
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, philox_rounds=rounds))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, philox_rounds=rounds,
+                checked="--checked" in sys.argv))

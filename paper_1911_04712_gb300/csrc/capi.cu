@@ -31,7 +31,11 @@ const char *dpd_last_error(void) { return dpd::last_error_text(); }
 #define DPD_STR2(x) #x
 #define DPD_STR(x) DPD_STR2(x)
 const char *dpd_version(void) {
+#if defined(DPD_CHECKED) && DPD_CHECKED
+  return "gb300-dpd 0.1 (sm_103a, Philox-4x32-" DPD_STR(DPD_PHILOX_ROUNDS) ", checked)";
+#else
   return "gb300-dpd 0.1 (sm_103a, Philox-4x32-" DPD_STR(DPD_PHILOX_ROUNDS) ")";
+#endif
 }
 
 int dpd_philox_rounds(void) { return DPD_PHILOX_ROUNDS; }

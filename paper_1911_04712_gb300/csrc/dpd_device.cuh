@@ -44,6 +44,19 @@ static_assert(kSlicesX >= 2 && kSlicesX * kMaxCellsPerAxis < (1 << kSliceBits),
 constexpr unsigned kErrNonFinite = 1u;        // a position or velocity is NaN/Inf
 constexpr unsigned kErrRunaway = 2u;          // a particle moved more than one box edge
 constexpr unsigned kErrSpecies = 4u;          // a loaded species outside 0..nspec-1
+constexpr unsigned kErrBounds = 8u;           // checked build: an index check failed
+
+// Checked build (-DDPD_CHECKED=1, libdpd_checked.so): the kernels test the
+// indices they derive from device data (cell indices, cell starts, list
+// entries, scatter targets) before using them; a failed test records
+// kErrBounds in the error word and the access is skipped, so nothing faults.
+// In the normal build DPD_IN_BOUNDS is the constant true and the tests
+// compile away.
+#if defined(DPD_CHECKED) && DPD_CHECKED
+#define DPD_IN_BOUNDS(cond, err) ((cond) || (atomicOr((err), ::dpd::kErrBounds), false))
+#else
+#define DPD_IN_BOUNDS(cond, err) true
+#endif
 
 // Constants of one periodic box (read-only during a step).
 struct BoxDev {

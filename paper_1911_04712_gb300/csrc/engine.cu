@@ -495,6 +495,7 @@ int Engine::update_params(const std::vector<BoxParams> &params) {
 
 int Engine::load_box(int box, const float *pos, const float *vel, bool device_ptr,
                      const int32_t *species) {
+  NvtxRange range("dpd load state");
   if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
   const int n = pbase_[box + 1] - pbase_[box];
   if (n == 0) return DPD_OK;
@@ -579,6 +580,7 @@ int Engine::capture_graph(int nsteps, cudaGraphExec_t *out) {
 }
 
 int Engine::step(int64_t nsteps) {
+  NvtxRange range("dpd step");
   if (nsteps < 0) return set_error(DPD_ERR_ARG, "nsteps must be >= 0");
   if (ntot_ == 0 || nsteps == 0) {
     for (auto &s : st_host_) {
@@ -670,6 +672,8 @@ int Engine::check_error() {
   DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
   if (h) {
     DPD_CUDA_TRY(cudaMemsetAsync(d_.err, 0, sizeof(unsigned), stream_));
+    if (h & kErrBounds)
+      return set_error(DPD_ERR_INTERNAL, "a kernel's index check failed (checked build)");
     if (h & kErrSpecies)
       return set_error(DPD_ERR_ARG, "a particle species is outside 0..nspec-1");
     return set_error(DPD_ERR_NUMERIC, "device flagged %s%s",
@@ -680,6 +684,7 @@ int Engine::check_error() {
 }
 
 int Engine::gather(int box, float *pos, float *vel, float *frc, bool device_ptr) {
+  NvtxRange range("dpd read state");
   if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
   const int n = pbase_[box + 1] - pbase_[box];
   if (n == 0) return DPD_OK;
@@ -762,6 +767,7 @@ int Engine::copy_box_raw(int box, float4 *pos, float4 *vel, float4 *frc, bool to
 }
 
 int Engine::box_sums(std::vector<double> &sums) {
+  NvtxRange range("dpd statistics");
   const int nb = nbox();
   if (work_dirty_) {
     int rc = build_work();
@@ -860,6 +866,7 @@ int Engine::init_box(int box, uint64_t seed) {
 
 int Engine::repack(const std::vector<BoxParams> &params, const std::vector<int64_t> &np,
                    const std::vector<int> &src) {
+  NvtxRange range("dpd repack");
   if (params.size() != np.size() || src.size() != np.size() || params.empty())
     return set_error(DPD_ERR_ARG, "repack: inconsistent sizes");
   const std::vector<int> old_pbase = pbase_;

@@ -10,10 +10,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dpd_device.cuh"
 #include "kernels.h"
 
 namespace dpd {
+
+// NVTX range over a host call: its launches and copies appear under this
+// name in a profiler's timeline (Nsight Systems, ncu --nvtx).  Header-only
+// NVTX; without a tool attached a range costs a few nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Records a message for dpd_last_error() and returns `code`.
 int set_error(int code, const char *fmt, ...);

@@ -114,6 +114,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   constexpr int U = kScanUnroll;
   constexpr int LS = BAL ? 1 : NT;  // list stride: own row of the warp scratch, or a column
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+  if (alive && !DPD_IN_BOUNDS(p >= 0 && p < P.ntot, P.err)) alive = false;
   if (alive) {
     pi = P.pos[p];
     vi = P.vel[p];
@@ -198,6 +199,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
   };
   auto pair = [&](uint32_t e, const float4 &qi, const float4 &ui) -> float4 {
     const int j = (int)(e & kSlotMask);
+    if (!DPD_IN_BOUNDS(j < P.ntot, P.err)) return make_float4(0.f, 0.f, 0.f, 0.f);
     return pair_at(e, __ldg(P.pos + j), __ldg(P.vel + j), qi, ui);
   };
 
@@ -276,11 +278,13 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
         if (t <= g) o += s;
       }
       const int offo = __shfl_sync(0xffffffffu, off, o);
-      if (g < total) {
+      if (g < total && DPD_IN_BOUNDS(g - offo >= 0 && g - offo < CAP, P.err)) {
         const uint32_t e = wl[(g - offo) * LS + o];
         const int j = (int)(e & kSlotMask);
-        const float4 r = pair_at(e, __ldg(P.pos + j), __ldg(P.vel + j), own[o], own[32 + o]);
-        atomicAdd(P.frc + pw + o, r);
+        if (DPD_IN_BOUNDS(j < P.ntot && pw + o >= 0 && pw + o < P.ntot, P.err)) {
+          const float4 r = pair_at(e, __ldg(P.pos + j), __ldg(P.vel + j), own[o], own[32 + o]);
+          atomicAdd(P.frc + pw + o, r);
+        }
       }
     }
     __syncwarp();  // lists may be refilled
@@ -303,6 +307,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
         return;
       }
     }
+    if (!DPD_IN_BOUNDS(cnt <= CAP, P.err)) cnt = 0;
     for (int k = 0; k < cnt; ++k) {
       const float4 g = pair(lst[k * LS], pi, vi);
       fx += g.x;
@@ -349,13 +354,17 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
       code |= kCodeIY;
     }
     const int rowbase = B.cellBase + (z * ny + y) * nx;
+    const bool row_ok = DPD_IN_BOUNDS(rowbase >= 0 && rowbase + nx <= P.ncell, P.err);
     // Slices xlo .. xhi of the row: one range of slots, or two across an x
     // face, where the far part is the image r_j - L (xlo < 0) or is seen
     // from r_i - L (xhi >= nx).  Half stencil, own row: forward from the
     // slot after p (pairs within one slice belong to the lower slot).
     const bool own = HALF && r == 0;
     const int lo = own ? cx : xlo, hi = xhi;
-    const int nseg = alive ? ((lo < 0 || hi >= nx) ? 2 : 1) : 0;
+    const int nseg =
+        (alive && row_ok && DPD_IN_BOUNDS(lo >= -nx && lo <= hi && hi < 2 * nx, P.err))
+            ? ((lo < 0 || hi >= nx) ? 2 : 1)
+            : 0;
     auto segment = [&](int sg, int &j0, int &j1, float &ax, float &jsx, uint32_t &c) {
       ax = pi.x;
       jsx = 0.f;
@@ -384,6 +393,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
         j0 = own ? p + 1 : __ldg(P.start + rowbase + lo);
         j1 = __ldg(P.start + rowbase + hi + 1);
       }
+      if (!DPD_IN_BOUNDS(j0 >= 0 && j0 <= j1 && j1 <= P.ntot, P.err)) j0 = j1 = 0;
     };
     int sg = 0, j = 0, j1 = 0;
     float ax = 0.f, jsx = 0.f;
@@ -392,6 +402,7 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     for (;;) {
       bool more = false;
       if (sg < nseg) {
+        if (!DPD_IN_BOUNDS(cnt <= CAP - U, P.err)) cnt = 0;
         const int stop = (c & (kCodeJX | kCodeJY | kCodeJZ))
                              ? scan_range<true, LS, CAP, U>(P.pos, j, j1, ax, ay, az, jsx, jsy, jsz,
                                                          rc2m1, c, lst, cnt)
@@ -606,6 +617,7 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
       R.ish |= kCodeIY;
     }
     R.rb = B.cellBase + (zz * ny + yy) * B.n[0];
+    if (!DPD_IN_BOUNDS(R.rb >= 0 && R.rb + B.n[0] <= P.ncell, P.err)) R.rb = 0;
     R.gMain = __ldg(P.start + R.rb + kSlicesX * m0);
     R.lenMain = __ldg(P.start + R.rb + kSlicesX * (m1 + 1)) - R.gMain;
     R.gBeg = 0;
@@ -643,6 +655,7 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
   // targets: the tile's own cells in the centre row (rows[4] is dy = dz = 0)
   const int t0 = __ldg(P.start + rows[4].rb + kSlicesX * cx0);
   const int t1 = __ldg(P.start + rows[4].rb + kSlicesX * (cx0 + nc));
+  if (!DPD_IN_BOUNDS(t0 >= 0 && t0 <= t1 && t1 <= P.ntot, P.err)) return;
 
   if (!staged) {
     // too many particles to stage: read neighbours from global memory
@@ -683,6 +696,7 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
       } else {
         g = R.gEnd + (i - R.lenBeg - R.lenMain);
       }
+      if (!DPD_IN_BOUNDS(g >= 0 && g < P.ntot, P.err)) g = 0;
       float4 q = __ldg(P.pos + g);
       q.x -= xs;
       q.y -= R.jsy;
@@ -706,7 +720,8 @@ __global__ void __launch_bounds__(kTileThreads) k_force_tiles(Packed P, TileGrid
     }
     int sx, cyy, czz;
     unpack_cell(__float_as_int(vi.w), sx, cyy, czz);
-    const int kt = sx / kSlicesX - cx0 + 1;  // virtual cell of the target, 1..nc
+    int kt = sx / kSlicesX - cx0 + 1;  // virtual cell of the target, 1..nc
+    if (alive && !DPD_IN_BOUNDS(kt >= 1 && kt <= nc, P.err)) kt = 1;
     const uint32_t idi = __float_as_uint(pi.w);
     float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
     int cnt = 0;

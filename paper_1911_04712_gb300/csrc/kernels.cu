@@ -192,7 +192,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Packed P, bool adva
 __global__ void __launch_bounds__(kBinThreads) k_bin_keys(Packed P) {
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
   if (p >= P.ntot) return;
-  P.keyTmp[P.start[P.cellOf[p]] + P.slotIn[p]] = p;
+  const int c = P.cellOf[p];
+  if (!DPD_IN_BOUNDS(c >= 0 && c < P.ncell, P.err)) return;
+  const int k = P.start[c] + P.slotIn[p];
+  if (!DPD_IN_BOUNDS(k >= 0 && k < P.ntot, P.err)) return;
+  P.keyTmp[k] = p;
 }
 
 // STABLE: a particle's place in its cell is its rank by previous slot among
@@ -204,14 +208,17 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(Packed P, bool zero
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
   if (p >= P.ntot) return;
   const int c = P.cellOf[p];
+  if (!DPD_IN_BOUNDS(c >= 0 && c < P.ncell, P.err)) return;
   const int s0 = P.start[c];
   int rank = P.slotIn[p];
   if constexpr (STABLE) {
     const int s1 = P.start[c + 1];
+    if (!DPD_IN_BOUNDS(s0 >= 0 && s0 <= s1 && s1 <= P.ntot, P.err)) return;
     rank = 0;
     for (int t = s0; t < s1; ++t) rank += (P.keyTmp[t] < p) ? 1 : 0;
   }
   const int dst = s0 + rank;
+  if (!DPD_IN_BOUNDS(dst >= s0 && dst < P.start[c + 1] && dst < P.ntot, P.err)) return;
   P.pos[dst] = P.pos2[p];
   P.vel[dst] = P.vel2[p];
   if (zero_frc) P.frc[dst] = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -135,6 +135,7 @@ __device__ __forceinline__ void integrate_one(const Packed &P, const BoxDev &B, 
   v.w = __int_as_float(pack_cell(cx, cy, cz));
   P.pos2[p] = x;
   P.vel2[p] = v;
+  if (!DPD_IN_BOUNDS(c >= 0 && c < P.ncell, P.err)) return;
   P.cellOf[p] = c;
   P.slotIn[p] = atomicAdd(P.count + c, 1);
 }

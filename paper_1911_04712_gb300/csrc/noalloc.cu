@@ -172,5 +172,13 @@ extern "C" int dpd_forces_noalloc(int64_t n, const float *pos, const float *vel,
   StepConfig cfg{};
   DPD_CUDA_TRY(launch_step(P, false, false, cfg, s));
   DPD_CUDA_TRY(launch_gather(P, 0, 0, (int)n, nullptr, nullptr, force, s));
+#if defined(DPD_CHECKED) && DPD_CHECKED
+  // checked build: read the error word back (the normal build does not wait)
+  unsigned h = 0;
+  DPD_CUDA_TRY(cudaMemcpyAsync(&h, P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  DPD_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h & kErrBounds)
+    return set_error(DPD_ERR_INTERNAL, "a kernel's index check failed (checked build)");
+#endif
   return DPD_OK;
 }

@@ -21,6 +21,7 @@ LIB_PATH = os.environ.get("DPD_LIBRARY") or os.path.join(HERE, "libdpd.so")
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_STATE, ERR_NUMERIC, ERR_TIMEOUT, ERR_BUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
+ERR_INTERNAL = -8  # checked build only: a kernel's index check failed
 WHERE_HOST, WHERE_DEVICE = 0, 1
 PARAM_KEXP, PARAM_MASS, PARAM_BODYFORCE, PARAM_POISEUILLE_F = 1, 2, 3, 4
 PARAM_FLOW_AXIS, PARAM_GRAD_AXIS, PARAM_STENCIL = 5, 6, 7
@@ -42,7 +43,8 @@ STAGE_NAMES = ("integrate_bin", "scan", "bin_keys", "bin_scatter", "force")
 
 _NAMES = {ERR_ARG: "DPD_ERR_ARG", ERR_NOMEM: "DPD_ERR_NOMEM", ERR_CUDA: "DPD_ERR_CUDA",
           ERR_STATE: "DPD_ERR_STATE", ERR_NUMERIC: "DPD_ERR_NUMERIC",
-          ERR_TIMEOUT: "DPD_ERR_TIMEOUT", ERR_BUSY: "DPD_ERR_BUSY"}
+          ERR_TIMEOUT: "DPD_ERR_TIMEOUT", ERR_BUSY: "DPD_ERR_BUSY",
+          ERR_INTERNAL: "DPD_ERR_INTERNAL"}
 
 
 class DPDError(RuntimeError):

@@ -266,3 +266,39 @@ def test_tuning_table_roundtrip_and_variants_agree(mods):
             assert np.array_equal(o, outs[0])
     finally:
         B.tuning_set(0, up0, var0)
+
+
+def test_full_mix_in_the_benchmark_configuration(mods):
+    """The 512-box mix at full size, packed and launched as the benchmark runs
+    it (half stencil, tuned packed tables): every box's momentum balance after
+    20 steps, and a sample of boxes against the oracle (forces at load within
+    1e-5 of the RMS, 20-step trajectories within 1e-3 rc)."""
+    D, B = mods
+    specs = box_mix(512, master_seed=0)
+    states = [uniform_box_state(s.L, rho=s.rho, kT=s.kT, seed=s.seed) for s in specs]
+    descs = [B.make_desc(s.L, len(st[0]), a=s.a, gamma=s.gamma, kT=s.kT, dt=s.dt, seed=s.seed)
+             for s, st in zip(specs, states)]
+    bt = B.Batch(descs, stencil=1)
+    for k, (x, v) in enumerate(states):
+        bt.set_state(k, x, v)
+    sample = np.random.default_rng(5).choice(len(specs), 6, replace=False)
+    f0 = {int(k): bt.get_forces(int(k)) for k in sample}
+    bt.step(20)
+    for k, (x, v) in enumerate(states):
+        _, vb = bt.get_state(k)
+        dP = vb.astype(np.float64).sum(0) - v.astype(np.float64).sum(0)
+        assert np.abs(dP).max() <= 1e-6 * np.abs(vb).sum() + 1e-6, k
+    for k in sample:
+        k = int(k)
+        s, (x, v) = specs[k], states[k]
+        p = O.Params(L=(s.L,) * 3, a=s.a, gamma=s.gamma, kT=s.kT, rc=1.0, dt=s.dt, seed=s.seed)
+        fr, _ = O.forces(p, x, v, 0, mode=O.MODE_CELLS)
+        rms = math.sqrt((fr ** 2).sum(1).mean())
+        assert np.abs(f0[k] - fr).max() <= 1e-5 * rms, k
+        st = O.State(p, x, v, mode=O.MODE_CELLS)
+        st.run(20)
+        xb, _ = bt.get_state(k)
+        d = xb.astype(np.float64) - st.x
+        d -= s.L * np.round(d / s.L)
+        assert np.abs(d).max() < 1e-3, k
+    bt.close()

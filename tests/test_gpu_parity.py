@@ -333,15 +333,19 @@ def test_non_finite_input_is_reported(dpd):
 
 
 # -------------------------------------------------- full-size sampled parity
+@pytest.mark.parametrize("stencil", [0, 1])
 @pytest.mark.parametrize("L", [64.0, 128.0])
-def test_full_size_forces_sampled(dpd, L):
+def test_full_size_forces_sampled(dpd, L, stencil):
+    """Full-size boxes in the launch configuration the benchmark times (the
+    half stencil with its tuned variant at L = 128) and with the full stencil:
+    sampled forces against the oracle, and properties that hold at any size."""
     x, v = uniform_box_state(L, rho=3, seed=0)
     p = _params(L, seed=0)
-    box = _box(dpd, p)
+    box = _box(dpd, p, stencil)
     box.set_state(x, v)
     box.step(3)                         # exercise binning at full size
     xg, vg = box.get_state()
-    box2 = _box(dpd, p)
+    box2 = _box(dpd, p, stencil)
     box2.set_state(xg, vg)
     fg = box2.get_forces()
     which = np.random.default_rng(1).choice(len(x), 1500, replace=False)
@@ -353,6 +357,13 @@ def test_full_size_forces_sampled(dpd, L):
     ssum = np.abs(fg.astype(np.float64).sum(0)).max()
     assert ssum <= 1e-6 * np.abs(fg).sum()
     assert np.all(xg >= 0) and np.all(xg < L)
+    # momentum balance over 20 more steps at full size
+    box.step(20)
+    _, v2 = box.get_state()
+    dP = v2.astype(np.float64).sum(0) - vg.astype(np.float64).sum(0)
+    assert np.abs(dP).max() <= 1e-6 * np.abs(v2).sum()
+    box.close()
+    box2.close()
 
 
 @pytest.mark.parametrize("tiling", [dict(tiles=0), dict(tiles=1), dict(tiles=1, tile_cells=1),
