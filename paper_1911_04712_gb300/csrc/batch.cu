@@ -265,7 +265,7 @@ int dpd_batch_get_state(dpd_batch *b, int box, float *pos, float *vel, int where
   if ((rc = batch_ready(b))) return rc;
   rc = b->eng.gather(b->slot[box], pos, vel, nullptr, where == DPD_WHERE_DEVICE);
   if (rc) return rc;
-  return b->eng.check_error();
+  return b->eng.take_error();
 }
 
 int dpd_batch_get_forces(dpd_batch *b, int box, float *force, int where) {
@@ -278,7 +278,7 @@ int dpd_batch_get_forces(dpd_batch *b, int box, float *force, int where) {
   if ((rc = batch_ready(b))) return rc;
   rc = b->eng.gather(b->slot[box], nullptr, nullptr, force, where == DPD_WHERE_DEVICE);
   if (rc) return rc;
-  return b->eng.check_error();
+  return b->eng.take_error();
 }
 
 int dpd_batch_get_stats(dpd_batch *b, dpd_stats *out) {
@@ -303,7 +303,7 @@ int dpd_batch_get_stats(dpd_batch *b, dpd_stats *out) {
     o.step = (int64_t)b->eng.box_state(k).step;
     o.n = n;
   }
-  return b->eng.check_error();
+  return b->eng.take_error();  // fetched with the sums
 }
 
 }  // extern "C"

@@ -270,7 +270,7 @@ int dpd_get_state(dpd_ctx *ctx, float *pos, float *vel, int where) {
     return dpd::set_error(DPD_ERR_ARG, "bad where");
   int rc = ctx->eng.gather(0, pos, vel, nullptr, where == DPD_WHERE_DEVICE);
   if (rc) return rc;
-  return ctx->eng.check_error();
+  return ctx->eng.take_error();
 }
 
 int dpd_get_forces(dpd_ctx *ctx, float *force, int where) {
@@ -281,7 +281,7 @@ int dpd_get_forces(dpd_ctx *ctx, float *force, int where) {
     return dpd::set_error(DPD_ERR_ARG, "bad where");
   int rc = ctx->eng.gather(0, nullptr, nullptr, force, where == DPD_WHERE_DEVICE);
   if (rc) return rc;
-  return ctx->eng.check_error();
+  return ctx->eng.take_error();
 }
 
 int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out) {
@@ -301,7 +301,7 @@ int dpd_get_stats(dpd_ctx *ctx, dpd_stats *out) {
   out->pressure = (double)n * out->kT / V + out->virial / (3.0 * V);
   out->step = (int64_t)ctx->eng.box_state(0).step;
   out->n = n;
-  return ctx->eng.check_error();
+  return ctx->eng.take_error();  // fetched with the sums
 }
 
 namespace {

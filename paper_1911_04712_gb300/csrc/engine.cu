@@ -133,6 +133,7 @@ Engine::~Engine() {
     drop_graph();
     free_all();
     if (d_.err) cudaFree(d_.err);
+    if (h_err_) cudaFreeHost(h_err_);
     if (d_tiles_) cudaFree(d_tiles_);
     if (d_mixed_) cudaFree(d_mixed_);
     for (void *q : {(void *)d_wbeg_, (void *)d_from_, (void *)d_acc_, (void *)d_spart_})
@@ -162,6 +163,8 @@ int Engine::init() {
   DPD_CUDA_TRY(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
   DPD_CUDA_TRY(cudaMalloc(&d_.err, sizeof(unsigned)));
   DPD_CUDA_TRY(cudaMemset(d_.err, 0, sizeof(unsigned)));
+  DPD_CUDA_TRY(cudaMallocHost(&h_err_, sizeof(unsigned)));
+  *h_err_ = 0u;
   return DPD_OK;
 }
 
@@ -667,9 +670,20 @@ int Engine::sync() {
 }
 
 int Engine::check_error() {
-  unsigned h = 0;
-  DPD_CUDA_TRY(cudaMemcpyAsync(&h, d_.err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+  int rc = fetch_error();
+  if (rc) return rc;
   DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
+  return take_error();
+}
+
+int Engine::fetch_error() {
+  DPD_CUDA_TRY(cudaMemcpyAsync(h_err_, d_.err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+  return DPD_OK;
+}
+
+int Engine::take_error() {
+  const unsigned h = *h_err_;
+  *h_err_ = 0u;
   if (h) {
     DPD_CUDA_TRY(cudaMemsetAsync(d_.err, 0, sizeof(unsigned), stream_));
     if (h & kErrBounds)
@@ -687,10 +701,11 @@ int Engine::gather(int box, float *pos, float *vel, float *frc, bool device_ptr)
   NvtxRange range("dpd read state");
   if (box < 0 || box >= nbox()) return set_error(DPD_ERR_ARG, "box index out of range");
   const int n = pbase_[box + 1] - pbase_[box];
-  if (n == 0) return DPD_OK;
   const Packed P = packed();
-  if (device_ptr) {
-    DPD_CUDA_TRY(launch_gather(P, box, pbase_[box], n, pos, vel, frc, stream_));
+  if (n == 0 || device_ptr) {
+    if (n > 0) DPD_CUDA_TRY(launch_gather(P, box, pbase_[box], n, pos, vel, frc, stream_));
+    int rc = fetch_error();
+    if (rc) return rc;
     DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
     return DPD_OK;
   }
@@ -706,6 +721,8 @@ int Engine::gather(int box, float *pos, float *vel, float *frc, bool device_ptr)
     DPD_CUDA_TRY(launch_gather(P, box, pbase_[box], n, nullptr, nullptr, sp, stream_));
     DPD_CUDA_TRY(cudaMemcpyAsync(frc, sp, bytes, cudaMemcpyDeviceToHost, stream_));
   }
+  int rc = fetch_error();
+  if (rc) return rc;
   DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
   return DPD_OK;
 }
@@ -787,6 +804,8 @@ int Engine::box_sums(std::vector<double> &sums) {
                             box_out));
   DPD_CUDA_TRY(cudaMemcpyAsync(h_sum_, box_out, nsum * sizeof(double), cudaMemcpyDeviceToHost,
                                stream_));
+  int rc = fetch_error();
+  if (rc) return rc;
   DPD_CUDA_TRY(cudaStreamSynchronize(stream_));
   sums.assign(h_sum_, h_sum_ + nsum);
   return DPD_OK;

@@ -122,6 +122,12 @@ class Engine {
   int profile(int64_t nsteps, double *stage_ms);
   int sync();
   int check_error();                // reads and clears the device error word
+  // The same in two halves, so that a read-out that synchronises anyway
+  // brings the error word back with its data: fetch_error() enqueues the
+  // copy to pinned memory, take_error() (after a synchronisation) reads and
+  // clears it.  gather() and box_sums() fetch; their callers take.
+  int fetch_error();
+  int take_error();
 
   int gather(int box, float *pos, float *vel, float *frc, bool device_ptr);
   // Raw slot-order copies of one box's pos / vel / frc (float4) to or from
@@ -192,6 +198,7 @@ class Engine {
   std::vector<int> wbeg_;            // first work item of each box (nbox + 1)
   int *d_wbeg_ = nullptr;
   double *h_sum_ = nullptr;  // pinned per-box statistics totals
+  unsigned *h_err_ = nullptr;  // pinned copy of the device error word
   size_t cap_hsum_ = 0;
   size_t cap_wbeg_ = 0;
   bool work_dirty_ = true;
