@@ -26,8 +26,9 @@
  * Step index of the noise: the force computed by dpd_set_state uses step 0;
  * the force computed during the k-th call-counted step uses step k.
  *
- * Arithmetic: FP32 state and forces; box-level reductions sum in FP64 (each
- * GPU thread's few terms as an error-free pair of FP32 numbers).
+ * Arithmetic: FP32 state and forces; box-level reductions sum in FP64 above
+ * the GPU block (inside a block of 4096 particles, as unevaluated pairs of
+ * FP32 numbers, about 2^-44 relative).
  *
  * Conventions for every call:
  *   - returns DPD_OK (0) or a negative DPD_ERR_* status; never aborts or
