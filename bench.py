@@ -54,6 +54,19 @@ def force_slots_per_particle(rho: float) -> float:
     return cands * CAND_SLOTS + pairs * PAIR_SLOTS
 
 
+# FP32 flops (an FMA counts 2) of the same work: a candidate's distance test
+# (3 subtractions, a multiply and two FMAs) and an interacting pair's r, w,
+# e . v_ij, the three terms and the update, the noise map included.
+CAND_FLOPS = 8
+PAIR_FLOPS = 30
+
+
+def force_flops_per_particle(rho: float) -> float:
+    cands = 27.0 * rho / 2.0
+    pairs = (4.0 * math.pi / 3.0) * rho / 2.0
+    return cands * CAND_FLOPS + pairs * PAIR_FLOPS
+
+
 # Algorithmic HBM bytes per particle-step of the streaming stages.  The
 # full stencil orders each cell by previous slot (key pass + ranked
 # reorder); the half stencil has no key pass and its reorder places by
@@ -442,6 +455,8 @@ def run_native(args):
         traffic = rec[0]
     slots = force_slots_per_particle(rho) * n
     achieved = slots / (force_ms / 1000.0) / 1e12
+    fp32_achieved = force_flops_per_particle(rho) * n / (force_ms / 1000.0) / 1e12
+    fp32_peak = 2.0 * alu_peak if alu_peak else None   # an FMA per lane per clock
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     stages = {}
     for name, t in zip(dpd.STAGE_NAMES, stage_ms):
@@ -530,7 +545,10 @@ def run_native(args):
                          "frac": (achieved / alu_peak) if alu_peak else None,
                          "traffic": traffic,
                          "peak_from": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_mhz} MHz "
-                                      f"({clock_src})"},
+                                      f"({clock_src})",
+                         "fp32": {"achieved": fp32_achieved, "peak": fp32_peak,
+                                  "unit": "TFLOP/s",
+                                  "frac": (fp32_achieved / fp32_peak) if fp32_peak else None}},
             "stages": stages,
             "stencils": stencils,
             "gpu_launches": dpd.kernels_per_step(args.stencil == "half") * args.steps,
