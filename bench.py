@@ -14,6 +14,10 @@ cell count, scan, stable reorder, pair forces with the Philox pair noise.
   roofline  the force kernel against the FP32/INT32 issue peak
             (SMs x 128 lanes x SM clock), timed with per-stage events
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+  batched, served, mixture, paper_benchmark
+            the 512-box mix, the served request stream, a binary mixture,
+            and the paper's own benchmark box (L = 64, rho = 8), each with
+            its own workload description
 
 `--impl reference` times the oracle alone (the reference arm of this build).
 With --gpus N > 1 (torchrun) every rank steps its own independent replica.
@@ -332,6 +336,40 @@ def run_mixture(args, stream):
             "kernel": "general force kernel (per-pair species tables)"}
 
 
+def run_paper_benchmark(args, stream):
+    """The paper's own benchmark (Sec. 5.1): one periodic box of L = 64 at
+    rho = 8 (2,097,152 particles) driven by the periodic Poiseuille force,
+    with the parameters of its weak-scaling runs (a = 50, gamma = 20, kT = 1,
+    dt = 0.002).  Its figure on one P100 (7.01 ms per step, 2.99e8
+    particle-steps/s) is context from other hardware, not a target."""
+    import torch
+
+    import paper_1911_04712_gb300.dpd as dpd
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+    L, rho, steps = 64.0, 8.0, args.paper_steps
+    x, v = uniform_box_state(L, rho=rho, seed=args.seed + 11)
+    n = len(x)
+    box = dpd.Box(L, a=50.0, gamma=20.0, kT=1.0, rc=1.0, dt=0.002, seed=args.seed,
+                  stream=stream, stencil=1 if args.stencil == "half" else 0)
+    box.set_param(dpd.PARAM_POISEUILLE_F, 0.05)
+    box.set_state(x, v)
+    box.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    box.close()
+    return {"workload": "the paper's periodic-Poiseuille benchmark: L=64, rho=8, a=50, "
+                        "gamma=20, kT=1, dt=0.002, periodic Poiseuille force f=0.05",
+            "particles": n, "steps": steps, "stencil": args.stencil, "unit": UNIT,
+            "value": n * steps / (ms * steps / 1000.0), "ms_per_step": ms,
+            "paper": {"value": 2.99e8, "ms_per_step": 7.01, "hardware": "1x P100",
+                      "note": "other hardware, context only"}}
+
+
 def run_served(args, rank=0, world=1):
     """Prefix of the served request stream: Poisson arrivals submitted in real
     time to one continuous-batching queue per GPU under a 120 GB HBM budget
@@ -524,6 +562,10 @@ def run_native(args):
     if not args.no_mixture:
         mixture = run_mixture(args, stream)
 
+    paper = None
+    if not args.no_paper_benchmark:
+        paper = run_paper_benchmark(args, stream)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.cpu_L, rho, args.cpu_steps)
@@ -558,6 +600,7 @@ def run_native(args):
             "batched": batched,
             "served": served,
             "mixture": mixture,
+            "paper_benchmark": paper,
         }
         print(json.dumps(out), flush=True)
     box.close()
@@ -588,6 +631,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-mixture", action="store_true")
+    ap.add_argument("--no-paper-benchmark", action="store_true")
+    ap.add_argument("--paper-steps", type=int, default=200)
     ap.add_argument("--mix-L", type=float, default=64.0)
     ap.add_argument("--mix-steps", type=int, default=200)
     ap.add_argument("--requests", type=int, default=200)
