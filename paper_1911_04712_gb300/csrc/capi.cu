@@ -185,7 +185,7 @@ int dpd_set_state_species(dpd_ctx *ctx, int64_t n, const float *pos, const float
                           const int32_t *species, int where) {
   dpd::clear_error();
   if (!ctx) return dpd::set_error(DPD_ERR_ARG, "null context");
-  if (n < 0 || n > (int64_t)(1 << 26)) return dpd::set_error(DPD_ERR_ARG, "bad particle count");
+  if (n < 0 || n > dpd::kMaxSlots) return dpd::set_error(DPD_ERR_ARG, "bad particle count");
   if (where != DPD_WHERE_HOST && where != DPD_WHERE_DEVICE)
     return dpd::set_error(DPD_ERR_ARG, "where must be DPD_WHERE_HOST or DPD_WHERE_DEVICE");
   if (n > 0 && (!pos || !vel)) return dpd::set_error(DPD_ERR_ARG, "null position or velocity");

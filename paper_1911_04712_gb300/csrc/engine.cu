@@ -39,7 +39,9 @@ int check_params(const BoxParams &bp, int n[3]) {
     n[k] = (int)nd * (k == 0 ? kSlicesX : 1);
     cells *= (double)n[k];
   }
-  if (cells > (double)(1 << 30)) return set_error(DPD_ERR_ARG, "too many cells (%g)", cells);
+  if (cells > (double)kMaxCellEntries)
+    return set_error(DPD_ERR_ARG, "too many cells (%g x-slices; at most %lld)", cells,
+                     kMaxCellEntries);
   auto nonneg = [](double v) { return std::isfinite(v) && v >= 0.0; };
   if (!nonneg(bp.a)) return set_error(DPD_ERR_ARG, "a must be >= 0");
   if (!nonneg(bp.gamma)) return set_error(DPD_ERR_ARG, "gamma must be >= 0");
@@ -451,7 +453,7 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
     boxes[b] = make_box_dev(params[b], (int)ctot, (int)ptot, (int)np[b]);
     ptot += np[b];
     ctot += (int64_t)n[0] * n[1] * n[2];
-    if (ptot >= (int64_t)(1 << 26) || ctot > (int64_t)(1 << 30))
+    if (ptot > kMaxSlots || ctot > kMaxCellEntries)
       return set_error(DPD_ERR_ARG, "packed set too large (%lld particles, %lld cells)",
                        (long long)ptot, (long long)ctot);
   }

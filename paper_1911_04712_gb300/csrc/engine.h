@@ -27,6 +27,11 @@ struct NvtxRange {
   NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Capacity of one packed set: particle slots are 26-bit indices in the pair
+// lists, and the cell starts (cells + 1 entries) fit one scan.
+constexpr long long kMaxSlots = 1LL << 26;
+constexpr long long kMaxCellEntries = (long long)kScanMaxTiles * kScanTile - 1;
+
 // Records a message for dpd_last_error() and returns `code`.
 int set_error(int code, const char *fmt, ...);
 void clear_error();

@@ -48,12 +48,16 @@ struct Resident {
   double t_submit, t_admit;
 };
 
+// Cell-list entries (x slices of the cells) of a request's box.
+int64_t request_cells(const BoxParams &bp) {
+  int64_t c = dpd::kSlicesX;
+  for (int k = 0; k < 3; ++k) c *= (int64_t)std::floor(bp.L[k] / bp.rc);
+  return c;
+}
+
 size_t request_bytes(const BoxParams &bp, int64_t n) {
-  int nc[3];
-  for (int k = 0; k < 3; ++k) nc[k] = (int)std::floor(bp.L[k] / bp.rc);
-  const size_t cells = (size_t)nc[0] * nc[1] * nc[2] * dpd::kSlicesX;  // cell-list entries
   // particle arrays (5 float4 + 3 int32) and cell arrays (2 int32), plus slack
-  return (size_t)n * (5 * 16 + 3 * 4) + cells * 2 * 4 + 4096;
+  return (size_t)n * (5 * 16 + 3 * 4) + (size_t)request_cells(bp) * 2 * 4 + 4096;
 }
 
 }  // namespace
@@ -179,7 +183,13 @@ static void worker_main(dpd_queue *q) {
         src.push_back((int)k);
         fresh.push_back(0);
       }
-      // admit waiting requests while the ledger and the box limit allow
+      // admit waiting requests while the ledger, the box limit and the packed
+      // set's slot and cell capacity allow
+      int64_t slots = 0, cells = 0;
+      for (const auto &r : next) {
+        slots += r.n;
+        cells += request_cells(r.bp);
+      }
       while (!q->pending.empty() && (int64_t)next.size() < q->opts.max_boxes) {
         auto it = q->pending.begin();
         if (q->opts.policy == 1)
@@ -188,6 +198,10 @@ static void worker_main(dpd_queue *q) {
                                   return (double)a.n * a.steps < (double)b.n * b.steps;
                                 });
         if (q->in_use + it->bytes > q->budget) break;
+        if (slots + it->n > dpd::kMaxSlots || cells + request_cells(it->bp) > dpd::kMaxCellEntries)
+          break;
+        slots += it->n;
+        cells += request_cells(it->bp);
         next.push_back(Resident{it->ticket, it->bp, it->n, it->steps, it->bytes, it->t_submit,
                                 q->now()});
         q->in_use += it->bytes;
@@ -335,7 +349,8 @@ int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket) {
     if (!(req->rho > 0)) return dpd::set_error(DPD_ERR_ARG, "give n > 0 or rho > 0");
     n = (int64_t)std::llround(req->rho * bp.L[0] * bp.L[1] * bp.L[2]);
   }
-  if (n < 2 || n >= (1 << 26)) return dpd::set_error(DPD_ERR_ARG, "particle count out of range");
+  if (n < 2 || n > dpd::kMaxSlots)
+    return dpd::set_error(DPD_ERR_ARG, "particle count out of range");
   const size_t bytes = request_bytes(bp, n);
   std::lock_guard<std::mutex> lk(q->mu);
   if (q->error) return dpd::set_error(q->error, "queue failed earlier: %s", q->error_text.c_str());

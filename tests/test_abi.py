@@ -58,6 +58,15 @@ def test_argument_errors_need_no_gpu(lib):
     assert dpd.lib().dpd_create(ctypes.byref(ctx), neg, -1.0, 4.5, 1.0, 1.0, 0.005, 0) == dpd.ERR_ARG
     assert dpd.lib().dpd_create(ctypes.byref(ctx), neg, 25.0, 4.5, 1.0, 1.0, 0.0, 0) == dpd.ERR_ARG
     assert dpd.lib().dpd_create(None, neg, 25.0, 4.5, 1.0, 1.0, 0.005, 0) == dpd.ERR_ARG
+    # a box whose cell list (2 x-slices per cell) exceeds one scan's 2^26 - 1 entries
+    huge = (ctypes.c_double * 3)(400.0, 400.0, 400.0)
+    assert dpd.lib().dpd_create(ctypes.byref(ctx), huge, 25.0, 4.5, 1.0, 1.0, 0.005, 0) == dpd.ERR_ARG
+    assert b"too many cells" in dpd.lib().dpd_last_error()
+    fits = (ctypes.c_double * 3)(300.0, 300.0, 300.0)   # 5.4e7 entries
+    rc = dpd.lib().dpd_create(ctypes.byref(ctx), fits, 25.0, 4.5, 1.0, 1.0, 0.005, 0)
+    assert rc != dpd.ERR_ARG
+    if rc == dpd.OK:
+        dpd.lib().dpd_destroy(ctx)
 
 
 def test_product_path_refuses_without_library(tmp_path, monkeypatch):

@@ -105,3 +105,18 @@ def test_bounded_wait_reports_timeout(S):
     with pytest.raises(D.DPDError):
         q.submit(S.make_request(8.0, rho=3, steps=10))
     q.close()
+
+
+def test_admission_respects_the_packed_set_capacity(S):
+    """Two runs that each fit one packed set but not together (2 x 4.1e7
+    particles against 2^26 particle slots) are admitted one after the other
+    and both complete, under a budget that would hold both."""
+    q = S.Queue(int(100e9), chunk_steps=2, stencil=1)
+    t = [q.submit(S.make_request(240.0, rho=3.0, seed=70 + k, steps=2)) for k in range(2)]
+    q.wait_all(600.0)
+    r = [q.result(x) for x in t]
+    q.close()
+    assert all(x["status"] == 0 for x in r), r
+    assert all(x["n"] == 41472000 for x in r)
+    first, second = sorted(r, key=lambda x: x["t_admit"])
+    assert second["t_admit"] >= first["t_done"] - 1e-6
