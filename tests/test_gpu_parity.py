@@ -366,6 +366,35 @@ def test_full_size_forces_sampled(dpd, L, stencil):
     box2.close()
 
 
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("L,rho,a,fb", [
+    (48.0, 3.0, 25.0, 0.05),              # the density sweep, with its Poiseuille force
+    (48.0, 5.0, 15.0, 0.05),
+    (48.0, 10.0, 7.5, 0.05),
+    ((47.3, 31.9, 20.6), 5.0, 40.0, 0.0),  # a served-stream-like box: non-integer edges
+])
+def test_workload_sizes_sampled_forces(dpd, L, rho, a, fb, stencil):
+    """Boxes at the sizes of the density sweep and of the served stream:
+    sampled forces after a few steps against the oracle, with the body
+    force and both stencils."""
+    x, v = uniform_box_state(L, rho=rho, seed=21)
+    kw = dict(fb=fb, fb_mode=O.FB_POISEUILLE, fb_flow=0, fb_grad=1) if fb else {}
+    p = _params(L, seed=21, a=a, **kw)
+    box = _box(dpd, p, stencil)
+    box.set_state(x, v)
+    box.step(4)
+    xg, vg = box.get_state()
+    box2 = _box(dpd, p, stencil)
+    box2.set_state(xg, vg)
+    fg = box2.get_forces()
+    which = np.random.default_rng(2).choice(len(x), 1000, replace=False)
+    f_ref = O.forces_subset(p, xg, vg, which, 0)
+    rms = math.sqrt((f_ref ** 2).sum(1).mean())
+    assert np.abs(fg[which].astype(np.float64) - f_ref).max() <= FORCE_TOL * rms
+    box.close()
+    box2.close()
+
+
 @pytest.mark.parametrize("tiling", [dict(tiles=0), dict(tiles=1), dict(tiles=1, tile_cells=1),
                                     dict(tiles=1, tile_cells=3), dict(tiles=1, tile_cells=5),
                                     dict(tiles=1, tile_cells=64),
