@@ -203,49 +203,79 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
     return pair_at(e, __ldg(P.pos + j), __ldg(P.vel + j), qi, ui);
   };
 
-  // Balanced drain: the warp's list entries are processed 32 at a time, one
-  // per lane whatever lane owns them; each owner then adds its results in
-  // list order, so every particle's sum has the same order as in the per-lane
-  // drain.
+  // Balanced drain.  Every lane first evaluates its own entries below M,
+  // the warp's mean list length (rounded down), in list order.  The entries
+  // beyond M of the longer lists are then processed 32 at a time, one per
+  // lane whatever lane owns them, through the warp scratch, and each owner
+  // adds those results after its own, again in list order.  So every
+  // particle's sum has the order of the per-lane drain (the same bits),
+  // while the lanes idle only on the short lists' shortfall below M.
   auto drain_balanced = [&]() {
     const int lane = threadIdx.x & 31;
-    int incl = cnt;
+    int all = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) all += __shfl_xor_sync(0xffffffffu, all, o);
+    if (all == 0) return;
+    const int M = all >> 5;
+    if (!DPD_IN_BOUNDS(cnt <= CAP, P.err)) cnt = 0;
+    const int ov = max(cnt - M, 0);  // this lane's entries M .. cnt - 1
+    int incl = ov;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
-    const int off = incl - cnt;
+    const int off = incl - ov;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) return;
     W->own_pos[lane] = make_float4(pi.x, pi.y, pi.z, __uint_as_float(idi));
     W->own_vel[lane] = vi;
+    // steps 0 .. M-1: own entries; then one step per chunk of 32 shared entries
+    const int nsteps = M + (total + 31) / 32;
     int carry = 0;
-    for (int base = 0; base < total; base += 32) {
-      W->start[lane] = -1;
-      __syncwarp();
-      if (cnt > 0 && off >= base && off < base + 32) W->start[off - base] = lane;
-      __syncwarp();
-      const unsigned starts = __ballot_sync(0xffffffffu, W->start[lane] >= 0);
-      const unsigned upto = starts & (0xffffffffu >> (31 - lane));
-      const int owner = upto ? W->start[31 - __clz(upto)] : carry;
-      const int offo = __shfl_sync(0xffffffffu, off, owner);
-      const int g = base + lane;
-      float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (g < total)
-        res = pair(W->list[owner * (CAP + 1) + (g - offo)], W->own_pos[owner], W->own_vel[owner]);
-      W->res[lane] = res;
-      __syncwarp();
-      const int lo = max(off - base, 0), hi = min(off + cnt - base, 32);
-      for (int q = lo; q < hi; ++q) {
-        const float4 t = W->res[q];
-        fx += t.x;
-        fy += t.y;
-        fz += t.z;
-        vir += t.w;
+    for (int t = 0; t < nsteps; ++t) {
+      const bool own_step = t < M;  // warp-uniform
+      uint32_t e = 0;
+      int who = lane;
+      bool valid;
+      if (own_step) {
+        valid = t < cnt;
+        if (valid) e = lst[t * LS];
+      } else {
+        const int base = (t - M) * 32;
+        W->start[lane] = -1;
+        __syncwarp();
+        if (ov > 0 && off >= base && off < base + 32) W->start[off - base] = lane;
+        __syncwarp();
+        const unsigned starts = __ballot_sync(0xffffffffu, W->start[lane] >= 0);
+        const unsigned upto = starts & (0xffffffffu >> (31 - lane));
+        who = upto ? W->start[31 - __clz(upto)] : carry;
+        carry = __shfl_sync(0xffffffffu, who, 31);
+        const int offo = __shfl_sync(0xffffffffu, off, who);
+        const int g = base + lane;
+        valid = g < total && DPD_IN_BOUNDS(M + (g - offo) < CAP, P.err);
+        if (valid) e = W->list[who * (CAP + 1) + M + (g - offo)];
       }
-      carry = __shfl_sync(0xffffffffu, owner, 31);
-      __syncwarp();
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) r = pair(e, W->own_pos[who], W->own_vel[who]);
+      if (own_step) {
+        fx += r.x;
+        fy += r.y;
+        fz += r.z;
+        vir += r.w;
+      } else {
+        const int base = (t - M) * 32;
+        W->res[lane] = r;
+        __syncwarp();
+        const int lo = max(off - base, 0), hi = min(off + ov - base, 32);
+        for (int q = lo; q < hi; ++q) {
+          const float4 u = W->res[q];
+          fx += u.x;
+          fy += u.y;
+          fz += u.z;
+          vir += u.w;
+        }
+        __syncwarp();
+      }
     }
     cnt = 0;
   };
