@@ -42,20 +42,39 @@ if ROOT not in sys.path:
 METRIC = "DPD particle-steps/s on 1 GB300, batched vs one-box-at-a-time; p50/p99 latency"
 UNIT = "particle-steps/s"
 
-# Algorithmic ALU issue slots of the force stage per particle-step, with each
+# Algorithmic ALU work of the force stage per particle-step, with each
 # candidate and each interacting pair counted once (what Newton's third law
-# leaves to do): a candidate test is 7 lane instructions (3 subtractions, a
-# multiply and two fused multiply-adds for r^2, one compare); an interacting
-# pair is 85 (about 25 FP32 instructions for r, w, e . v_ij and the force
-# update, and 60 integer instructions for Philox-4x32-10 and the noise map).
+# leaves to do): 27 rho / 2 candidates and (4 pi / 3) rho / 2 pairs.  A
+# candidate test is 7 FP32-pipe instructions (3 subtractions, a multiply and
+# two fused multiply-adds for r^2, one compare); a pair is 30 FP32-pipe
+# instructions (r, w, e . v_ij, the three terms, the update, the noise map)
+# plus one Philox-4x32-10 word.  The roofline weighs the Philox word by the
+# measured issue rates: FMA-equivalent work = FP32 instructions + words x
+# (FMA rate / Philox word rate), against the measured FMA rate.  (Survey
+# count for comparison: 7 slots per candidate and 110 per pair -- 30 FP32 and
+# 80 integer -- against SMs x 128 lanes x clock.)
 CAND_SLOTS = 7
-PAIR_SLOTS = 85
+PAIR_FP32 = 30
+SURVEY_PAIR_SLOTS = 110
+
+
+def force_counts(rho: float):
+    cands = 27.0 * rho / 2.0                 # 27-cell stencil, each pair once
+    pairs = (4.0 * math.pi / 3.0) * rho / 2.0
+    return cands, pairs
 
 
 def force_slots_per_particle(rho: float) -> float:
-    cands = 27.0 * rho / 2.0                 # 27-cell stencil, each pair once
-    pairs = (4.0 * math.pi / 3.0) * rho / 2.0
-    return cands * CAND_SLOTS + pairs * PAIR_SLOTS
+    """The survey's unweighted count (lane-instruction slots per particle)."""
+    cands, pairs = force_counts(rho)
+    return cands * CAND_SLOTS + pairs * SURVEY_PAIR_SLOTS
+
+
+def force_fma_equiv_per_particle(rho: float, fma_rate: float, philox_rate: float) -> float:
+    """FMA-equivalent work per particle with the Philox word weighed by the
+    measured rates."""
+    cands, pairs = force_counts(rho)
+    return cands * CAND_SLOTS + pairs * (PAIR_FP32 + fma_rate / philox_rate)
 
 
 # FP32 flops (an FMA counts 2) of the same work: a candidate's distance test
@@ -177,18 +196,26 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(L: float, rho: float, steps: int, seed: int = 0) -> dict:
-    """The FP64 oracle (cell-list mode, OpenMP over the host cores) on a
-    bounded sample: a box of the same recipe, `steps` steps after the initial force."""
+def cpu_baseline(L: float, rho: float, steps: int, seed: int = 0, threads: int = 0) -> dict:
+    """The FP64 oracle (cell-list mode, OpenMP over the host cores, or
+    `threads` of them) on a bounded sample: a box of the same recipe, `steps`
+    steps after the initial force."""
     import oracle as O
     from paper_1911_04712_gb300.workloads import uniform_box_state
     x, v = uniform_box_state(L, rho=rho, seed=seed)
     p = O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=seed)
-    st = O.State(p, x, v, mode=O.MODE_CELLS)
-    t0 = time.perf_counter()
-    st.run(steps)
-    dt = time.perf_counter() - t0
-    return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": O.num_threads(),
+    prev = O.num_threads()
+    if threads:
+        O.set_num_threads(threads)
+    try:
+        cores = O.num_threads()
+        st = O.State(p, x, v, mode=O.MODE_CELLS)
+        t0 = time.perf_counter()
+        st.run(steps)
+        dt = time.perf_counter() - t0
+    finally:
+        O.set_num_threads(prev)
+    return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"L={L:g} box of the same recipe ({x.shape[0]} particles, rho={rho:g}), "
                       f"{steps} step(s) after the initial force, FP64 cell-list mode"}
@@ -215,7 +242,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * elapsed / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"dpd_periodic_box_L{args.L:g}_rho{args.rho:g}",
+        "config": {"workload": f"oracle_sample_L{L_sample:g}_rho{args.rho:g}",
+                   "sample_of": f"dpd_periodic_box_L{args.L:g}_rho{args.rho:g}",
                    "reference_sample_L": L_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                          "sample": n},
@@ -458,6 +486,15 @@ def run_native(args):
             dist.barrier()
 
     clocks = ClockSampler(local).start() if not args.no_clocks else None
+    # measured issue rates for the force kernel's roofline, then about a
+    # second of untimed steps so that the clock samples see the GPU under
+    # this load through the timed region
+    rates = dpd.issue_rates(stream)
+    if clocks:
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 1.0:
+            box.step(20)
+            torch.cuda.synchronize()
     # ---- device-resident timed region
     barrier()
     torch.cuda.synchronize()
@@ -469,32 +506,38 @@ def run_native(args):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
+    # ---- per-stage events (same workload, same stream) for the roofline
+    stage_ms = box.profile(args.steps)
     clk = clocks.stop() if clocks else None
+    if clk:
+        clk["window"] = "sampled every 200 ms from before a 1 s untimed load through the timed region and the per-stage profile"
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = n * args.steps * world / (ms / 1000.0)
 
-    # ---- per-stage events (same workload, same stream) for the roofline
-    stage_ms = box.profile(args.steps)
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median")
-    clock_src = "median SM clock sampled during the timed region"
+    clock_src = "median SM clock sampled under load"
     if not (clk or {}).get("sm_mhz"):
         clock_src = "median SM clock under load from MEASURED_PEAKS.json"
-    alu_peak = sms * 128 * float(sm_mhz) * 1e6 / 1e12 if sm_mhz else None   # T lane-ops/s
+    lane_peak = sms * 128 * float(sm_mhz) * 1e6 / 1e12 if sm_mhz else None   # T lane-ops/s
     force_ms = stage_ms[4]
+    force_s = force_ms / 1000.0
     traffic = None
     rec = TRAFFIC.get((args.stencil, float(L), float(rho)))
     if rec and rec[1] == kernel_hash() and args.philox_rounds == 10:
         traffic = rec[0]
-    slots = force_slots_per_particle(rho) * n
-    achieved = slots / (force_ms / 1000.0) / 1e12
-    fp32_achieved = force_flops_per_particle(rho) * n / (force_ms / 1000.0) / 1e12
-    fp32_peak = 2.0 * alu_peak if alu_peak else None   # an FMA per lane per clock
+    fma_rate, phx_rate = rates["fma_lane_ops_per_s"], rates["philox_words_per_s"]
+    work = force_fma_equiv_per_particle(rho, fma_rate, phx_rate) * n
+    achieved = work / force_s / 1e12
+    peak = fma_rate / 1e12
+    survey_achieved = force_slots_per_particle(rho) * n / force_s / 1e12
+    fp32_achieved = force_flops_per_particle(rho) * n / force_s / 1e12
+    fp32_peak = 2.0 * peak
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     stages = {}
     for name, t in zip(dpd.STAGE_NAMES, stage_ms):
@@ -569,6 +612,7 @@ def run_native(args):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(args.cpu_L, rho, args.cpu_steps)
+        base["single_core"] = cpu_baseline(32.0, rho, 3, threads=1)
 
     if rank == 0:
         out = {
@@ -583,14 +627,20 @@ def run_native(args):
                        f"({48 * n / 1e6:.0f} MB of float4 x, v, f)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "kernel": "force", "achieved": achieved,
-                         "peak": alu_peak, "unit": "T lane-ops/s",
-                         "frac": (achieved / alu_peak) if alu_peak else None,
-                         "traffic": traffic,
-                         "peak_from": f"{sms} SMs x 128 FP32/INT32 lanes x {sm_mhz} MHz "
-                                      f"({clock_src})",
+                         "peak": peak, "unit": "T FMA-equivalent lane-ops/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_from": "measured on this GPU by dpd_issue_rates: FP32 FMA "
+                                      f"{fma_rate / 1e12:.2f} T lane-ops/s, Philox-4x32-10 "
+                                      f"{phx_rate / 1e12:.4f} T words/s (1 word = "
+                                      f"{fma_rate / phx_rate:.1f} FMA slots)",
+                         "work_per_particle": force_fma_equiv_per_particle(rho, fma_rate, phx_rate),
+                         "survey_count": {"achieved": survey_achieved, "peak": lane_peak,
+                                          "unit": "T lane-ops/s",
+                                          "frac": (survey_achieved / lane_peak) if lane_peak else None,
+                                          "peak_from": f"{sms} SMs x 128 lanes x {sm_mhz} MHz "
+                                                       f"({clock_src})"},
                          "fp32": {"achieved": fp32_achieved, "peak": fp32_peak,
-                                  "unit": "TFLOP/s",
-                                  "frac": (fp32_achieved / fp32_peak) if fp32_peak else None}},
+                                  "unit": "TFLOP/s", "frac": fp32_achieved / fp32_peak}},
             "stages": stages,
             "stencils": stencils,
             "gpu_launches": dpd.kernels_per_step(args.stencil == "half") * args.steps,

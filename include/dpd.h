@@ -256,7 +256,7 @@ DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uin
  * table.  Contexts and batches pick their variants when their state is
  * laid out.  The package's autotuner measures the variants per band on the
  * GPU and sets the tables. */
-#define DPD_NUM_FORCE_VARIANTS 13
+#define DPD_NUM_FORCE_VARIANTS 14
 #define DPD_MAX_DENSITY_BANDS 8
 #define DPD_TUNING_PACKED 2
 /* threads per block and list capacity of variant v; DPD_ERR_ARG if out of range */
@@ -265,6 +265,15 @@ DPD_API int dpd_force_variant_info(int v, int *threads, int *list_capacity);
 DPD_API int dpd_tuning_set(int table, int nbands, const double *rho_upper, const int *variant);
 /* copy at most `max` bands of the table in use; *nbands receives its length */
 DPD_API int dpd_tuning_get(int table, int max, double *rho_upper, int *variant, int *nbands);
+
+/* Measured issue rates on the current device, for the force kernel's
+ * roofline (the paper has no counterpart): rates[0] FP32 fused
+ * multiply-adds per second (lane operations, register-only loops, eight
+ * resident blocks of 256 threads per SM), rates[1] Philox-4x32-R words per
+ * second (the pair-noise generator).  Each is timed with CUDA events on
+ * `stream` (NULL = legacy default) over one launch of a few milliseconds
+ * after a warm-up launch; synchronises the stream.  Allocates 1 KB. */
+DPD_API int dpd_issue_rates(double rates[2], void *stream);
 
 /* ============================================================ many boxes */
 /* A batch steps many independent periodic boxes together: their particles
@@ -386,8 +395,20 @@ typedef struct {
 DPD_API int dpd_queue_create(dpd_queue **out, size_t hbm_budget_bytes, const dpd_queue_opts *opts);
 /* Stop the worker (the current chunk finishes) and release everything. */
 DPD_API int dpd_queue_destroy(dpd_queue *q);
-/* Non-blocking; thread-safe.  *ticket identifies the run. */
+/* Non-blocking; thread-safe.  *ticket identifies the run.  Its initial
+ * state is drawn on the device from req->seed: uniform positions in the
+ * box, velocities of variance kT/m with the mean removed. */
 DPD_API int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket);
+/* As dpd_queue_submit, with the caller's initial state: pos, vel are
+ * req->n x 3 FP32 HOST arrays (req->n > 0; particle i has id i), copied
+ * before the call returns (the caller keeps ownership).  keep_final != 0
+ * keeps the run's final state for dpd_queue_final_state. */
+DPD_API int dpd_queue_submit_state(dpd_queue *q, const dpd_request *req, const float *pos,
+                                   const float *vel, int keep_final, uint64_t *ticket);
+/* The final state of a finished run submitted with keep_final: n x 3 FP32
+ * HOST arrays in id order, full-step velocities.  DPD_ERR_BUSY until the
+ * run has finished, DPD_ERR_STATE if it kept no state. */
+DPD_API int dpd_queue_final_state(dpd_queue *q, uint64_t ticket, float *pos, float *vel);
 DPD_API int dpd_queue_poll(dpd_queue *q, uint64_t ticket, int *done);
 /* DPD_ERR_BUSY until the run has finished. */
 DPD_API int dpd_queue_result(dpd_queue *q, uint64_t ticket, dpd_result *out);
@@ -419,7 +440,13 @@ DPD_API int dpd_queue_get_stats(dpd_queue *q, dpd_queue_stats *out);
  * capture.  Work is enqueued on `stream` (NULL = legacy default) and the
  * call returns without synchronising.  All calls share the one scratch
  * array: calls whose work overlaps on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+ * threads) race and must be serialised by the caller.  Because the call
+ * does not wait for its work, a non-finite input position or velocity is
+ * not reported by the normal build (the forces come back non-finite or
+ * wrapped to 0); the checked build reads the device error word back and
+ * reports failed index checks.  The scratch address of each device is
+ * kept for the life of the process, so the call is not supported after
+ * cudaDeviceReset on that device. */
 #define DPD_NOALLOC_MAX_PARTICLES 32768
 #define DPD_NOALLOC_MAX_CELLS 32767
 DPD_API int dpd_forces_noalloc(int64_t n, const float *pos, const float *vel, const double box[3],

@@ -10,7 +10,7 @@ import os
 import numpy as np
 
 BATCH_GRAPH_CHUNK = 100
-NUM_FORCE_VARIANTS = 13
+NUM_FORCE_VARIANTS = 14
 TUNING_PACKED = 2
 # tuning tables: single box (full, half stencil) and packed sets of boxes
 TABLES = (("full", 0), ("half", 1), ("full_packed", 2), ("half_packed", 3))

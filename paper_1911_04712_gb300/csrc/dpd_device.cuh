@@ -45,6 +45,8 @@ constexpr unsigned kErrNonFinite = 1u;        // a position or velocity is NaN/I
 constexpr unsigned kErrRunaway = 2u;          // a particle moved more than one box edge
 constexpr unsigned kErrSpecies = 4u;          // a loaded species outside 0..nspec-1
 constexpr unsigned kErrBounds = 8u;           // checked build: an index check failed
+constexpr unsigned kErrCapacity = 16u;        // brick force kernel: one cell row's stencil
+                                              // holds more particles than its staging
 
 // Checked build (-DDPD_CHECKED=1, libdpd_checked.so): the kernels test the
 // indices they derive from device data (cell indices, cell starts, list

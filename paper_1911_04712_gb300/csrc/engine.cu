@@ -138,6 +138,7 @@ Engine::~Engine() {
     if (h_err_) cudaFreeHost(h_err_);
     if (d_tiles_) cudaFree(d_tiles_);
     if (d_mixed_) cudaFree(d_mixed_);
+    if (d_bricks_) cudaFree(d_bricks_);
     for (void *q : {(void *)d_wbeg_, (void *)d_from_, (void *)d_acc_, (void *)d_spart_})
       if (q) cudaFree(q);
     if (h_sum_) cudaFreeHost(h_sum_);
@@ -222,10 +223,15 @@ int Engine::build_bands() {
     const int table = cfg_.stencil + (nb > 1 ? 2 : 0);  // packed sets have their own table
     const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(table, rho);
     const int g = B.noise != 0 || B.nspec > 1;  // general kernel
-    if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g)
+    if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g) {
       runs.back().slot1 = pbase_[b + 1];
-    else
-      runs.push_back(ForceBand{pbase_[b], pbase_[b + 1], v, g});
+      runs.back().item1 = brick_beg_[b + 1];
+    } else {
+      ForceBand fb{pbase_[b], pbase_[b + 1], v, g};
+      fb.item0 = brick_beg_[b];
+      fb.item1 = brick_beg_[b + 1];
+      runs.push_back(fb);
+    }
   }
   if ((int)runs.size() > kMaxBands) {
     // too fragmented (boxes not ordered by band): one launch with the
@@ -238,6 +244,8 @@ int Engine::build_bands() {
     }
     const int best = (int)(std::max_element(cover.begin(), cover.end()) - cover.begin());
     runs.assign(1, ForceBand{0, ntot_, best, anyg});
+    runs[0].item0 = 0;
+    runs[0].item1 = (int)bricks_h_.size();
   }
   // Packed sets: the warps of each band whose slots span two boxes (the
   // device tests the same: the box of the first and of the last slot, the
@@ -339,6 +347,84 @@ int Engine::build_tiles() {
     cfg_.grid.tpr = 0;
     cfg_.grid.ntiles = (int)tiles_h_.size();
   }
+  return DPD_OK;
+}
+
+// Brick shape of a box: the target rows (by x bz) that stage the fewest
+// particles per target while a chunk of several slices still fits the
+// staging capacity at the box's mean density (the kernel narrows a chunk
+// where the density is higher, and splits a brick into rows where even one
+// slice does not fit).
+static void brick_shape(const BoxDev &B, int caps, int *by_out, int *bz_out, int *w_out) {
+  const double V = (double)B.L[0] * B.L[1] * B.L[2];
+  const double ps = (double)B.np / V * V / ((double)B.n[0] * B.n[1] * B.n[2]);  // per slice
+  double best = 1e300;
+  int by = 1, bz = 1, wb = 1;
+  for (int y = 1; y <= std::min(kBrickMaxBY, B.n[1]); ++y)
+    for (int z = 1; z <= std::min(kBrickMaxBZ, B.n[2]); ++z) {
+      const int nrows = (y + 2) * (z + 1);
+      int w = (int)std::floor(0.75 * caps / (nrows * std::max(ps, 1e-3))) - 4;
+      w = std::min(std::min(w, kBrickWMax), B.n[0]);
+      if (w < 2) continue;
+      const double ov = (double)nrows * (w + 4) / ((double)y * z * w);
+      if (ov < best - 1e-9) {
+        best = ov;
+        by = y;
+        bz = z;
+        wb = w;
+      }
+    }
+  *by_out = by;
+  *bz_out = bz;
+  *w_out = wb;
+}
+
+int Engine::build_bricks() {
+  const int nb = nbox();
+  const int caps = 896;
+  bricks_h_.clear();
+  brick_beg_.assign(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    brick_beg_[b] = (int)bricks_h_.size();
+    const BoxDev &B = boxes_[b];
+    if (B.np <= 0) continue;
+    int by, bz, w;
+    brick_shape(B, caps, &by, &bz, &w);
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int nby = (ny + by - 1) / by, nbz = (nz + bz - 1) / bz;
+    // x pieces of about 2048 targets, at least two chunks wide
+    const double ps = (double)B.np / ((double)nx * ny * nz);
+    int xs = (int)std::lround(2048.0 / std::max(by * bz * ps, 1e-3));
+    xs = std::max(std::min(xs, nx), std::min(2 * w, nx));
+    const int npx = (nx + xs - 1) / xs;
+    for (int kz = 0, z0 = 0; kz < nbz; ++kz) {
+      const int bzk = nz / nbz + (kz < nz % nbz ? 1 : 0);
+      for (int ky = 0, y0 = 0; ky < nby; ++ky) {
+        const int byk = ny / nby + (ky < ny % nby ? 1 : 0);
+        for (int kx = 0, s0 = 0; kx < npx; ++kx) {
+          const int len = nx / npx + (kx < nx % npx ? 1 : 0);
+          bricks_h_.push_back(make_int4(b, y0 | (byk << 16), z0 | (bzk << 16), s0 | ((s0 + len) << 16)));
+          s0 += len;
+        }
+        y0 += byk;
+      }
+      z0 += bzk;
+    }
+  }
+  brick_beg_[nb] = (int)bricks_h_.size();
+  if (bricks_h_.size() > cap_bricks_) {
+    if (d_bricks_) cudaFree(d_bricks_);
+    d_bricks_ = nullptr;
+    cap_bricks_ = 0;
+    DPD_CUDA_TRY(cudaMalloc(&d_bricks_, bricks_h_.size() * sizeof(int4)));
+    cap_bricks_ = bricks_h_.size();
+  }
+  if (!bricks_h_.empty())
+    DPD_CUDA_TRY(cudaMemcpyAsync(d_bricks_, bricks_h_.data(), bricks_h_.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, stream_));
+  cfg_.bricks.items = d_bricks_;
+  cfg_.bricks.nitems = (int)bricks_h_.size();
+  cfg_.bricks.caps = caps;
   return DPD_OK;
 }
 
@@ -474,6 +560,7 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
   DPD_CUDA_TRY(cudaMemcpyAsync(d_.pbase, pbase_.data(), pbase_.size() * sizeof(int),
                                cudaMemcpyHostToDevice, stream_));
   int rc2 = build_tiles();
+  if (!rc2) rc2 = build_bricks();
   if (!rc2) rc2 = build_bands();
   if (!rc2) rc2 = build_work();
   if (!rc2 && sample_every_ > 0) rc2 = ensure_sampling_buffers();
@@ -692,6 +779,10 @@ int Engine::take_error() {
       return set_error(DPD_ERR_INTERNAL, "a kernel's index check failed (checked build)");
     if (h & kErrSpecies)
       return set_error(DPD_ERR_ARG, "a particle species is outside 0..nspec-1");
+    if (h & kErrCapacity)
+      return set_error(DPD_ERR_NUMERIC,
+                       "local density beyond the brick force kernel's staging capacity "
+                       "(select another force variant)");
     return set_error(DPD_ERR_NUMERIC, "device flagged %s%s",
                      (h & kErrNonFinite) ? "non-finite positions/velocities " : "",
                      (h & kErrRunaway) ? "a particle moving more than one box edge per step" : "");

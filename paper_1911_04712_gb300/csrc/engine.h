@@ -190,6 +190,13 @@ class Engine {
   size_t cap_tiles_ = 0;
   int build_tiles();
   int build_bands();
+  // Work items of the brick force kernel for every box (brick_beg_[b] ..
+  // brick_beg_[b + 1] are box b's).
+  int build_bricks();
+  std::vector<int4> bricks_h_;
+  std::vector<int> brick_beg_;
+  int4 *d_bricks_ = nullptr;
+  size_t cap_bricks_ = 0;
   int variant_override_ = -1;
   bool fuse_ = true;
   bool fused_steps() const;  // fusion applies to this engine's steps now

@@ -846,10 +846,13 @@ struct VariantInfo {
   int threads, cap;
 };
 // Variants 7..9 use the balanced drain, 10..12 the spread drain (half
-// stencil; with the full stencil they run the per-lane drain).
+// stencil; with the full stencil they run the per-lane drain); 13 is the
+// brick kernel staged through shared memory (half stencil; with the full
+// stencil it runs variant 0).
 static const VariantInfo kVariants[kNumForceVariants] = {
     {128, 24}, {128, 16}, {128, 32}, {256, 24}, {64, 24}, {64, 32}, {256, 32},
-    {64, 24}, {128, 24}, {256, 24}, {64, 32}, {128, 32}, {128, 24}};
+    {64, 24}, {128, 24}, {256, 24}, {64, 32}, {128, 32}, {128, 24},
+    {kBrickThreads, kBrickListCap}};
 
 int force_variant_info(int v, int *threads, int *cap) {
   if (v < 0 || v >= kNumForceVariants) return -1;
@@ -901,7 +904,9 @@ size_t tile_smem_bytes(int stage_cap) {
 cudaError_t prepare_device() {
   // staged tiles may use more than the default 48 KB of dynamic shared memory
   const int maxb = 200 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_force_tiles<true>,
+  cudaError_t e = prepare_brick();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_force_tiles<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_force_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -926,6 +931,11 @@ cudaError_t launch_force(const Packed &P, const StepConfig &cfg, cudaStream_t s,
   const int nb = cfg.nbands > 0 ? cfg.nbands : 1;
   for (int k = 0; k < nb; ++k) {
     const ForceBand &b = bands[k];
+    if (half && !b.gauss && b.variant == kBrickVariant && cfg.nbands > 0 && cfg.bricks.items) {
+      const cudaError_t e = launch_force_brick(P, cfg.bricks, b.item0, b.item1, s);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (single) {
       if (half)
         launch_variant<true, true>(b.variant, b.gauss, P, b.slot0, b.slot1, false, s);

@@ -40,6 +40,27 @@ struct TileGrid {
   int stage_cap;  // staged particles per block (positions + velocities)
 };
 
+// Brick force kernel (half stencil, brick.cu): one block per work item
+// {box, y0 | by << 16, z0 | bz << 16, s0 | s1 << 16}, target rows y0 .. y0+by-1
+// and z0 .. z0+bz-1 over x slices [s0, s1), staged through shared memory
+// in chunks of at most kBrickWMax slices.
+constexpr int kBrickThreads = 256;
+constexpr int kBrickMaxBY = 4, kBrickMaxBZ = 4;
+constexpr int kBrickMaxRows = (kBrickMaxBY + 2) * (kBrickMaxBZ + 1);
+constexpr int kBrickWMax = 32;
+constexpr int kBrickListCap = 24;
+constexpr int kBrickMaxCaps = 1024;  // staged particles per block, at most
+constexpr int kBrickVariant = 13;    // the force variant that selects it
+struct BrickGrid {
+  const int4 *items;  // device, ordered by box
+  int nitems;
+  int caps;           // staged particles per block
+};
+size_t brick_smem_bytes(int caps);
+cudaError_t prepare_brick();
+cudaError_t launch_force_brick(const Packed &P, const BrickGrid &G, int i0, int i1,
+                               cudaStream_t s);
+
 // A contiguous slot range whose force kernel uses one variant.
 struct ForceBand {
   int slot0, slot1, variant;
@@ -48,9 +69,10 @@ struct ForceBand {
   // StepConfig::mixed_warps[mw_off ..]); warp-cooperative variants skip them
   // and a second launch runs them with the per-lane drain
   int mw_off, mw_count;
+  int item0, item1;  // the band's brick work items (brick variant)
 };
 constexpr int kMaxBands = 8;
-constexpr int kNumForceVariants = 13;
+constexpr int kNumForceVariants = 14;
 
 // How a step is launched.
 struct StepConfig {
@@ -60,6 +82,7 @@ struct StepConfig {
   int nbands = 0;        // 0: one band over every slot with variant 0
   ForceBand band[kMaxBands]{};
   const int *mixed_warps = nullptr;  // device: first slots of the bands' two-box warps
+  BrickGrid bricks{};                // work items of the brick force kernel
 };
 // Whether the variant drains over the whole warp (balanced or spread): such
 // kernels evaluate other lanes' entries with their own box's parameters.

@@ -76,7 +76,9 @@ __global__ void k_noalloc_reset(int ncell_padded, unsigned long long step) {
   }
 }
 
-// Device address of the scratch on each device, looked up once per device.
+// Device address of the scratch on each device, looked up once per device
+// and kept for the life of the process (a cudaDeviceReset, which may load
+// the module again at another address, is not supported).
 static unsigned char *scratch_address(int device, int *status) {
   static std::mutex mu;
   static unsigned char *addr[64] = {nullptr};

@@ -6,8 +6,9 @@
 // the boxes that reached their step count (reading their accumulated
 // statistics into results) and admits waiting requests while the HBM ledger
 // and the resident-box limit allow, then repacks the survivors and the new
-// boxes into one layout.  A new box's initial state is drawn on the device
-// from its seed.  Every box is stepped and sampled at its own step indices,
+// boxes into one layout.  A new box's initial state is the caller's (copied
+// at submission by dpd_queue_submit_state) or drawn on the device from its
+// seed.  Every box is stepped and sampled at its own step indices,
 // so a request's result does not depend on what else was resident.
 #include <algorithm>
 #include <chrono>
@@ -16,6 +17,7 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -32,12 +34,17 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// A caller's initial state (n x 3 positions then n x 3 velocities, host).
+using InitState = std::shared_ptr<const std::vector<float>>;
+
 struct Pending {
   uint64_t ticket;
   BoxParams bp;
   int64_t n, steps;
   size_t bytes;
   double t_submit;
+  InitState init;          // null: drawn on the device from the seed
+  bool keep_final = false;  // keep the final state for dpd_queue_final_state
 };
 
 struct Resident {
@@ -46,6 +53,8 @@ struct Resident {
   int64_t n, steps;
   size_t bytes;
   double t_submit, t_admit;
+  InitState init;
+  bool keep_final = false;
 };
 
 // Cell-list entries (x slices of the cells) of a request's box.
@@ -73,6 +82,7 @@ struct dpd_queue {
   std::deque<Pending> pending;
   std::vector<Resident> resident;  // engine box order
   std::unordered_map<uint64_t, dpd_result> done;
+  std::unordered_map<uint64_t, std::vector<float>> finals;  // kept final states (id order)
   std::unordered_map<uint64_t, int> state;  // 0 pending, 1 resident, 2 done
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -203,7 +213,7 @@ static void worker_main(dpd_queue *q) {
         slots += it->n;
         cells += request_cells(it->bp);
         next.push_back(Resident{it->ticket, it->bp, it->n, it->steps, it->bytes, it->t_submit,
-                                q->now()});
+                                q->now(), it->init, it->keep_final});
         q->in_use += it->bytes;
         q->state[it->ticket] = 1;
         q->admitted++;
@@ -225,7 +235,12 @@ static void worker_main(dpd_queue *q) {
       rc = q->eng.repack(params, np, src);
       for (size_t k = 0; rc == DPD_OK && k < next.size(); ++k) {
         if (!fresh[k]) continue;
-        rc = q->eng.init_box((int)k, next[k].bp.seed);
+        if (next[k].init) {
+          const float *x = next[k].init->data();
+          rc = q->eng.load_box((int)k, x, x + 3 * next[k].n, false);
+        } else {
+          rc = q->eng.init_box((int)k, next[k].bp.seed);
+        }
         if (rc == DPD_OK) {
           q->eng.set_box_state((int)k, 0, next[k].steps);
           q->eng.set_sample_from((int)k, next[k].steps / 2);
@@ -249,11 +264,19 @@ static void worker_main(dpd_queue *q) {
     const double dt = std::chrono::duration<double>(Clock::now() - tc).count();
     // read out the boxes that reached their step count
     std::vector<std::pair<int, std::vector<double>>> outs;
+    std::vector<std::pair<uint64_t, std::vector<float>>> fin;
     for (int k = 0; rc == DPD_OK && k < q->eng.nbox(); ++k) {
       if (q->eng.box_state(k).remaining <= 0) {
         std::vector<double> acc(fields);
         rc = q->eng.read_acc(k, acc.data());
         outs.emplace_back(k, std::move(acc));
+        if (rc == DPD_OK && q->resident[k].keep_final) {
+          const int64_t n = q->resident[k].n;
+          std::vector<float> xv((size_t)(6 * n));
+          rc = q->eng.gather(k, xv.data(), xv.data() + 3 * n, nullptr, false);
+          if (rc == DPD_OK) rc = q->eng.take_error();
+          fin.emplace_back(q->resident[k].ticket, std::move(xv));
+        }
       }
     }
     std::lock_guard<std::mutex> lk(q->mu);
@@ -263,6 +286,7 @@ static void worker_main(dpd_queue *q) {
     }
     q->busy_s += dt;
     q->particle_steps += ps;
+    for (auto &f : fin) q->finals[f.first] = std::move(f.second);
     for (auto &o : outs) finish_locked(q, q->resident[o.first], o.second.data(), DPD_OK);
     if (!outs.empty()) q->cv_done.notify_all();
   }
@@ -322,7 +346,10 @@ int dpd_queue_destroy(dpd_queue *q) {
   return DPD_OK;
 }
 
-int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket) {
+}  // extern "C"
+
+static int submit(dpd_queue *q, const dpd_request *req, const float *pos, const float *vel,
+                  bool keep_final, uint64_t *ticket) {
   dpd::clear_error();
   if (!q || !req || !ticket) return dpd::set_error(DPD_ERR_ARG, "null argument");
   BoxParams bp{};
@@ -351,6 +378,15 @@ int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket) {
   }
   if (n < 2 || n > dpd::kMaxSlots)
     return dpd::set_error(DPD_ERR_ARG, "particle count out of range");
+  InitState init;
+  if (pos || vel) {
+    if (!pos || !vel) return dpd::set_error(DPD_ERR_ARG, "give both positions and velocities");
+    if (req->n <= 0) return dpd::set_error(DPD_ERR_ARG, "a caller's state needs n > 0");
+    auto v = std::make_shared<std::vector<float>>((size_t)(6 * n));
+    std::memcpy(v->data(), pos, (size_t)n * 3 * sizeof(float));
+    std::memcpy(v->data() + 3 * n, vel, (size_t)n * 3 * sizeof(float));
+    init = v;
+  }
   const size_t bytes = request_bytes(bp, n);
   std::lock_guard<std::mutex> lk(q->mu);
   if (q->error) return dpd::set_error(q->error, "queue failed earlier: %s", q->error_text.c_str());
@@ -358,10 +394,43 @@ int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket) {
     return dpd::set_error(DPD_ERR_NOMEM, "request needs %zu bytes, budget is %zu", bytes,
                           q->budget);
   const uint64_t t = q->next_ticket++;
-  q->pending.push_back(Pending{t, bp, n, req->steps, bytes, q->now()});
+  q->pending.push_back(Pending{t, bp, n, req->steps, bytes, q->now(), init, keep_final});
   q->state[t] = 0;
   *ticket = t;
   q->cv.notify_all();
+  return DPD_OK;
+}
+
+extern "C" {
+
+int dpd_queue_submit(dpd_queue *q, const dpd_request *req, uint64_t *ticket) {
+  return submit(q, req, nullptr, nullptr, false, ticket);
+}
+
+int dpd_queue_submit_state(dpd_queue *q, const dpd_request *req, const float *pos,
+                           const float *vel, int keep_final, uint64_t *ticket) {
+  if (!pos || !vel) {
+    dpd::clear_error();
+    return dpd::set_error(DPD_ERR_ARG, "null position or velocity array");
+  }
+  return submit(q, req, pos, vel, keep_final != 0, ticket);
+}
+
+int dpd_queue_final_state(dpd_queue *q, uint64_t ticket, float *pos, float *vel) {
+  dpd::clear_error();
+  if (!q || !pos || !vel) return dpd::set_error(DPD_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(q->mu);
+  auto it = q->state.find(ticket);
+  if (it == q->state.end()) return dpd::set_error(DPD_ERR_ARG, "unknown ticket");
+  if (it->second != 2) return dpd::set_error(DPD_ERR_BUSY, "request %llu not finished",
+                                             (unsigned long long)ticket);
+  auto f = q->finals.find(ticket);
+  if (f == q->finals.end())
+    return dpd::set_error(DPD_ERR_STATE, "request %llu kept no final state",
+                          (unsigned long long)ticket);
+  const size_t half = f->second.size() / 2;
+  std::memcpy(pos, f->second.data(), half * sizeof(float));
+  std::memcpy(vel, f->second.data() + half, half * sizeof(float));
   return DPD_OK;
 }
 

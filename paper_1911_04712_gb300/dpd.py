@@ -143,6 +143,17 @@ def version() -> str:
     return lib().dpd_version().decode()
 
 
+def issue_rates(stream=None) -> dict:
+    """Measured FP32 FMA lane-ops/s and Philox words/s of the current device
+    (register-only loops timed with CUDA events; dpd_issue_rates)."""
+    L = lib()
+    L.dpd_issue_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    L.dpd_issue_rates.restype = ctypes.c_int
+    r = (ctypes.c_double * 2)()
+    check(L.dpd_issue_rates(r, _stream_ptr(stream)))
+    return {"fma_lane_ops_per_s": r[0], "philox_words_per_s": r[1]}
+
+
 def philox_rounds() -> int:
     """Rounds of the loaded library's Philox-4x32-R noise generator."""
     L = lib()
@@ -386,18 +397,36 @@ def forces_noalloc(pos, vel, L, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, see
     """Pair forces from a caller-held CUDA state through dpd_forces_noalloc,
     which allocates no device memory (its scratch is a static device array).
 
-    pos, vel: n x 3 float32 CUDA tensors; returns (or fills ``out``) an n x 3
-    CUDA tensor.  The work is enqueued on ``stream`` without synchronising."""
+    pos, vel: n x 3 CUDA tensors on one device (copied to contiguous float32
+    if they are not); ``out``, if given, must be a contiguous float32 n x 3
+    tensor on the same device.  The work is enqueued on ``stream`` (default:
+    torch's current stream of that device) without synchronising; the call
+    runs with that device current, whose scratch array it uses."""
     import torch
     if not (_is_cuda_tensor(pos) and _is_cuda_tensor(vel)):
         raise ValueError("pos and vel must be CUDA tensors")
+    dev = pos.device
+    if vel.device != dev:
+        raise ValueError("pos and vel must be on the same device")
     n = int(pos.shape[0])
-    pp, _, kp = _vec3_arg(pos, n)
-    vv, _, kv = _vec3_arg(vel, n)
-    if out is None:
-        out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
-    L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
-    box = (ctypes.c_double * 3)(*L3)
-    check(lib().dpd_forces_noalloc(n, pp, vv, box, a, gamma, kT, rc, dt, int(seed), int(step),
-                                   ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    if out is not None:
+        if not (_is_cuda_tensor(out) and out.device == dev and out.dtype == torch.float32
+                and out.is_contiguous() and tuple(out.shape) == (n, 3)):
+            raise ValueError("out must be a contiguous float32 (n, 3) tensor on pos.device")
+    with torch.cuda.device(dev):
+        pp, _, kp = _vec3_arg(pos, n)
+        vv, _, kv = _vec3_arg(vel, n)
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        L3 = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+        box = (ctypes.c_double * 3)(*L3)
+        check(lib().dpd_forces_noalloc(n, pp, vv, box, a, gamma, kT, rc, dt, int(seed),
+                                       int(step), ctypes.c_void_p(out.data_ptr()),
+                                       _stream_ptr(st)))
+        if isinstance(st, torch.cuda.Stream):
+            # converted copies stay allocated until the enqueued work has read them
+            for t in (kp, kv):
+                if t is not pos and t is not vel:
+                    t.record_stream(st)
     return out

@@ -53,6 +53,9 @@ def _declare(L):
     L.dpd_queue_create.argtypes = [c.POINTER(vp), c.c_size_t, c.POINTER(QueueOpts)]
     L.dpd_queue_destroy.argtypes = [vp]
     L.dpd_queue_submit.argtypes = [vp, c.POINTER(Request), c.POINTER(c.c_uint64)]
+    L.dpd_queue_submit_state.argtypes = [vp, c.POINTER(Request), vp, vp, c.c_int,
+                                         c.POINTER(c.c_uint64)]
+    L.dpd_queue_final_state.argtypes = [vp, c.c_uint64, vp, vp]
     L.dpd_queue_poll.argtypes = [vp, c.c_uint64, c.POINTER(c.c_int)]
     L.dpd_queue_result.argtypes = [vp, c.c_uint64, c.POINTER(Result)]
     L.dpd_queue_cancel.argtypes = [vp, c.c_uint64]
@@ -60,7 +63,7 @@ def _declare(L):
     L.dpd_queue_get_stats.argtypes = [vp, c.POINTER(QueueStats)]
     for name in ("dpd_queue_create", "dpd_queue_destroy", "dpd_queue_submit", "dpd_queue_poll",
                  "dpd_queue_result", "dpd_queue_cancel", "dpd_queue_wait_all",
-                 "dpd_queue_get_stats"):
+                 "dpd_queue_get_stats", "dpd_queue_submit_state", "dpd_queue_final_state"):
         getattr(L, name).restype = c.c_int
     return L
 
@@ -117,6 +120,28 @@ class Queue:
         t = ctypes.c_uint64()
         _check(_lib().dpd_queue_submit(self._q, ctypes.byref(req), ctypes.byref(t)))
         return t.value
+
+    def submit_state(self, req: Request, pos, vel, keep_final: bool = False) -> int:
+        """Submit with the caller's initial state (n x 3 float32 host arrays,
+        req.n = n); keep_final keeps the final state for final_state()."""
+        x = np.ascontiguousarray(pos, dtype=np.float32)
+        v = np.ascontiguousarray(vel, dtype=np.float32)
+        if x.shape != (req.n, 3) or v.shape != (req.n, 3):
+            raise ValueError("pos and vel must be n x 3 with n = req.n")
+        t = ctypes.c_uint64()
+        _check(_lib().dpd_queue_submit_state(self._q, ctypes.byref(req),
+                                             x.ctypes.data_as(ctypes.c_void_p),
+                                             v.ctypes.data_as(ctypes.c_void_p),
+                                             int(bool(keep_final)), ctypes.byref(t)))
+        return t.value
+
+    def final_state(self, ticket: int, n: int):
+        """(positions, velocities) of a finished run kept with keep_final."""
+        x = np.empty((n, 3), dtype=np.float32)
+        v = np.empty((n, 3), dtype=np.float32)
+        _check(_lib().dpd_queue_final_state(self._q, ticket, x.ctypes.data_as(ctypes.c_void_p),
+                                            v.ctypes.data_as(ctypes.c_void_p)))
+        return x, v
 
     def done(self, ticket: int) -> bool:
         d = ctypes.c_int()

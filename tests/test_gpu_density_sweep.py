@@ -1,9 +1,12 @@
 """Density sweep with the periodic Poiseuille force (Sec. 4.2): flow along x,
 force -f for y <= L/2 and +f above, f = 0.05, 2000 steps.
 
-* L = 12, rho = 3: the GPU and the oracle start from the same state; their
-  trajectories decorrelate (the dynamics is chaotic) so the time-averaged
-  velocity profiles are compared within their statistical error.
+* L = 12, rho = 3, and the full-size L = 48, rho = 3 box: the GPU and the
+  oracle start from the same state; their trajectories decorrelate (the
+  dynamics is chaotic) so the time-averaged velocity profiles (48 slabs at
+  L = 48) are compared within their statistical error.  The oracle's cost
+  grows with the density: rho = 5 and 10 at L = 48 would take it 8 and 30
+  minutes on the host cores, so those two run on the GPU alone (below).
 * L = 48, rho = 3 / 5 / 10 (a = 25 / 15 / 7.5), GPU only: 2000 steps are 10
   time units, far below the viscous time (L/2)^2 / nu, so away from the two
   planes where the force switches each half moves as a plug, v_x = -/+ f t
@@ -70,6 +73,38 @@ def test_startup_profile_matches_oracle_statistically(dpd):
     # and both show the driven profile: negative below L/2, positive above
     for prof in (gpu.mean(0), ref.mean(0)):
         assert prof[: nb // 2].mean() < -0.1 and prof[nb // 2:].mean() > 0.1
+
+
+def test_full_size_profile_matches_oracle_rho3(dpd):
+    """L = 48, rho = 3, a = 25 (331,776 particles), 2000 steps: the GPU and
+    the FP64 oracle (cell-list mode, OpenMP) from the same state; the 48-slab
+    profiles averaged over the second 1000 steps (50 samples) agree within
+    5 sqrt(2) standard errors, and both show the plug flow -/+ f t."""
+    L, nb = 48.0, 48
+    x, v = uniform_box_state(L, rho=3, seed=5)
+    box = _box(dpd, L, 25.0, 5)
+    box.set_state(x, v)
+    p = O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=1.0, dt=0.005, seed=5, fb=F0,
+                 fb_mode=O.FB_POISEUILLE, fb_flow=0, fb_grad=1)
+    st = O.State(p, x, v, mode=O.MODE_CELLS)
+    box.step(1000)
+    st.run(1000)
+    gpu, ref = [], []
+    for _ in range(50):
+        box.step(20)
+        st.run(20)
+        xg, vg = box.get_state()
+        gpu.append(_profile(xg, vg, L, nb))
+        ref.append(_profile(st.x, st.v, L, nb))
+    gpu, ref = np.array(gpu).mean(0), np.array(ref).mean(0)
+    n_bin = len(x) / nb
+    sigma = np.sqrt(1.0 / n_bin) / np.sqrt(10.0)   # about 10 independent samples in 1000 steps
+    diff = gpu - ref
+    assert np.all(np.abs(diff) < 5 * np.sqrt(2) * sigma), (np.abs(diff).max(), sigma)
+    t = (1000 + 510) * 0.005    # mean time of the 50 samples
+    for prof in (gpu, ref):     # plug flow away from the switching planes
+        assert np.all(np.abs(prof[6:nb // 2 - 6] + F0 * t) < 0.15 * F0 * t + 0.05)
+        assert np.all(np.abs(prof[nb // 2 + 6:nb - 6] - F0 * t) < 0.15 * F0 * t + 0.05)
 
 
 @pytest.mark.parametrize("rho,a", [(3, 25.0), (5, 15.0), (10, 7.5)])

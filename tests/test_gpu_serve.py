@@ -120,3 +120,100 @@ def test_admission_respects_the_packed_set_capacity(S):
     assert all(x["n"] == 41472000 for x in r)
     first, second = sorted(r, key=lambda x: x["t_admit"])
     assert second["t_admit"] >= first["t_done"] - 1e-6
+
+
+def _oracle_params(L, seed, fb):
+    import oracle as O
+    return O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=seed,
+                    fb=fb, fb_mode=O.FB_POISEUILLE, fb_flow=0, fb_grad=1)
+
+
+def _near_face_counts(y, L, nbins, tol):
+    """Per slab: particles within tol (in slab widths) of one of its faces."""
+    u = np.asarray(y, np.float64) / L * nbins
+    k = np.round(u).astype(int)
+    hit = np.abs(u - k) < tol
+    c = np.zeros(nbins)
+    np.add.at(c, k[hit] % nbins, 1)          # the slab above the face
+    np.add.at(c, (k[hit] - 1) % nbins, 1)    # the slab below
+    return c
+
+
+def test_served_run_matches_the_oracle(S):
+    """A run given its initial state, stepped inside a mix with short chunks
+    and repacks (three resident slots, other runs admitted and retired around
+    it), against the FP64 oracle run from the same state: the sampled mean
+    kT and pressure, the slab profile of the flow velocity (Sec. 4.2), and
+    the final state (within 1e-3 rc)."""
+    import oracle as O
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+    L, seed, fb = 8.0, 11, 0.3
+    steps, every, nbins = 60, 10, 8
+    x0, v0 = uniform_box_state(L, rho=3, seed=seed)
+    n = len(x0)
+    req = S.make_request(L, n=n, a=25.0, gamma=4.5, kT=1.0, seed=seed, steps=steps,
+                         body_force=fb, body_mode=2, flow_axis=0, grad_axis=1)
+    q = S.Queue(1 << 30, max_boxes=3, chunk_steps=7, sample_every=every, nbins=nbins)
+    others = [q.submit(r) for r in _reqs(S, 3, 3)]
+    t = q.submit_state(req, x0, v0, keep_final=True)
+    others += [q.submit(r) for r in _reqs(S, 4, 3)]
+    q.wait_all(300)
+    got = q.result(t)
+    xg, vg = q.final_state(t, n)
+    assert all(q.result(k)["status"] == 0 for k in others)
+    q.close()
+    assert got["status"] == 0 and got["samples"] == 3      # steps 40, 50, 60
+
+    st = O.State(_oracle_params(L, seed, fb), x0, v0)
+    kts, prs, sums, cnts = [], [], np.zeros(nbins), np.zeros(nbins)
+    near = np.zeros(nbins)     # particles near a slab face at a sample, per adjacent slab
+    for s in range(every, steps + 1, every):
+        st.run(every)
+        if s > steps // 2:
+            d = st.stats()
+            kts.append(d["kT"])
+            prs.append(d["pressure"])
+            prof, cnt = st.profile(nbins)
+            sums += prof * cnt
+            cnts += cnt
+            near += _near_face_counts(st.x[:, 1], L, nbins, 1e-4)
+    assert got["kT_mean"] == pytest.approx(np.mean(kts), rel=1e-4)
+    assert got["pressure_mean"] == pytest.approx(np.mean(prs), rel=1e-4)
+    # the FP32 and FP64 trajectories differ by ~1e-6 rc here: a particle within
+    # 1e-4 of a face may sit in either slab, which moves a pooled slab mean by
+    # at most 2 max|v| / count; every other difference must be round-off
+    allow = 1e-3 + near * 2.0 * np.abs(st.v[:, 0]).max() * 1.5 / cnts
+    assert np.all(np.abs(got["profile"] - sums / cnts) <= allow), (got["profile"], sums / cnts)
+    assert (near == 0).sum() >= nbins // 2
+    d = xg.astype(np.float64) - st.x
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < 1e-3
+    assert np.abs(vg.astype(np.float64) - st.v).max() < 1e-2
+
+
+def test_served_profile_bins_equal_the_oracle_on_the_sampled_state(S):
+    """One sample taken at the last step, whose state is read back: the
+    device's slab sums (k_sample) and kT against the oracle's profile and
+    statistics on that same state, bin by bin."""
+    import oracle as O
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+    L, seed, fb, nbins = 7.5, 5, 0.2, 6
+    x0, v0 = uniform_box_state(L, rho=3, seed=seed)
+    n = len(x0)
+    req = S.make_request(L, n=n, seed=seed, steps=2, body_force=fb, body_mode=2,
+                         flow_axis=0, grad_axis=1)
+    q = S.Queue(1 << 30, chunk_steps=100, sample_every=1, nbins=nbins)
+    t = q.submit_state(req, x0, v0, keep_final=True)
+    q.wait_all(120)
+    got = q.result(t)
+    xg, vg = q.final_state(t, n)
+    q.close()
+    assert got["samples"] == 1
+    p = O.Params(L=(L, L, L), seed=seed, fb=fb, fb_mode=O.FB_POISEUILLE, fb_flow=0, fb_grad=1)
+    st = O.State(p, xg, vg)
+    prof, cnt = st.profile(nbins)
+    # the device bins in FP32: only a particle within ~1e-6 of a face can differ
+    near = _near_face_counts(xg[:, 1], L, nbins, 1e-5)
+    allow = 1e-12 + near * 2.0 * np.abs(vg[:, 0]).max() * 1.5 / cnt
+    assert np.all(np.abs(got["profile"] - prof) <= allow), (got["profile"], prof)
+    assert got["kT_mean"] == pytest.approx(st.stats()["kT"], rel=1e-12)

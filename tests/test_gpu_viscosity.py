@@ -102,3 +102,56 @@ def test_viscosity_matches_table1(dpd, params, eta_range):
     lo, hi = eta_range
     nearest = min(max(eta, lo), hi)
     assert abs(eta / nearest - 1) < 0.05, eta
+
+
+def test_periodic_poiseuille_figure_setup(dpd):
+    """The set-up of the paper's periodic Poiseuille figure (Sec. 4.2):
+    L = 64, rho = 8, a = 10, gamma = 20, kT = 1, k = 0.5, dt = 0.005, force
+    along z switching sign at x = L/2.  The figure gives no force magnitude;
+    f = 0.01 keeps the peak velocity near 0.5.  Started on the parabola of
+    a guessed eta (19, the dissipative kinetic-theory value for these
+    parameters, 2 pi gamma rho^2 / 15 * int_0^1 r^4 (1 - r)^(2k) dr = 17.9,
+    plus a kinetic part), run for three relaxation times of the slowest
+    mode, then averaged over two: the 64-slab profile of v_z(x) is the
+    parabola rho f (x L/2 - x^2) / (2 eta) of each half within 3 % of its
+    peak (more than 2 rc from the planes where the force switches), and
+    both halves give the same eta."""
+    L, rho, a, gamma, kT, k, dt, f = 64.0, 8, 10.0, 20.0, 1.0, 0.5, 0.005, 0.01
+    nb, eta0 = 64, 19.0
+    x, v = uniform_box_state(L, rho=rho, kT=kT, seed=23)
+    v = v.copy()
+    v[:, 2] += (rho * f / (2 * eta0)) * _shape(x[:, 0].astype(np.float64), L).astype(np.float32)
+    box = dpd.Box(L, a=a, gamma=gamma, kT=kT, rc=1.0, dt=dt, seed=23, kexp=k)
+    box.set_param(dpd.PARAM_FLOW_AXIS, 2)
+    box.set_param(dpd.PARAM_GRAD_AXIS, 0)
+    box.set_param(dpd.PARAM_POISEUILLE_F, f)
+    box.set_state(x, v)
+    t_relax = (L / (2 * np.pi)) ** 2 / (eta0 / rho)
+    box.step(int(3 * t_relax / dt))
+    every = 200
+    prof, cnt = np.zeros(nb), np.zeros(nb)
+    for _ in range(int(2 * t_relax / dt) // every):
+        box.step(every)
+        xg, vg = box.get_state()
+        b = np.clip((xg[:, 0] / L * nb).astype(int), 0, nb - 1)
+        prof += np.bincount(b, weights=vg[:, 2].astype(np.float64), minlength=nb)
+        cnt += np.bincount(b, minlength=nb)
+    box.close()
+    prof /= cnt
+    xc = (np.arange(nb) + 0.5) * L / nb
+    g = _shape(xc, L)
+    c = (g * prof).sum() / (g * g).sum()
+    eta = rho * f / (2 * c)
+    lo, hi = slice(0, nb // 2), slice(nb // 2, nb)
+    eta_lo = rho * f / (2 * (g[lo] * prof[lo]).sum() / (g[lo] ** 2).sum())
+    eta_hi = rho * f / (2 * (g[hi] * prof[hi]).sum() / (g[hi] ** 2).sum())
+    peak = np.abs(c * g).max()
+    # away from the two planes where the force switches (2 rc on each side,
+    # where the stresses' finite range rounds the kink of the parabolas)
+    far = np.minimum(np.abs(xc - L / 2), np.minimum(xc, L - xc)) > 2.0
+    resid = np.abs(prof - c * g)[far].max()
+    print(f"Sec. 4.2 figure set-up: eta = {eta:.3f} (halves {eta_lo:.3f}, {eta_hi:.3f}), "
+          f"peak velocity {peak:.3f}, max deviation from the parabola {resid / peak:.3%}")
+    assert abs(eta_lo / eta_hi - 1) < 0.03
+    assert resid < 0.03 * peak
+    assert 12.0 < eta < 30.0

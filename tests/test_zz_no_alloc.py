@@ -59,11 +59,19 @@ def test_noalloc_forces_match_allocating_path_two_calls(dpd):
 
 def test_noalloc_repeated_call_is_unchanged_and_rejects_large_inputs(dpd):
     import torch
+    import oracle as O
     x, v = uniform_box_state(6.0, rho=3, seed=3)
     xd, vd = torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda()
     f1 = dpd.forces_noalloc(xd, vd, 6.0, seed=3, step=5).cpu().numpy()
     f2 = dpd.forces_noalloc(xd, vd, 6.0, seed=3, step=5).cpu().numpy()
     assert np.array_equal(f1, f2)
+    # the step reaches the pair noise: the FP64 oracle's forces at step 5
+    p = O.Params(L=(6.0, 6.0, 6.0), a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.005, seed=3)
+    want, _ = O.forces(p, x, v, 5)
+    rms = math.sqrt((want ** 2).sum(1).mean())
+    assert np.abs(f1.astype(np.float64) - want).max() <= FORCE_TOL * rms
+    with pytest.raises(ValueError):                 # an output of the wrong dtype
+        dpd.forces_noalloc(xd, vd, 6.0, out=torch.empty_like(xd, dtype=torch.float16))
     big = torch.zeros((dpd.NOALLOC_MAX_PARTICLES + 1, 3), dtype=torch.float32, device="cuda")
     with pytest.raises(dpd.DPDError) as ei:
         dpd.forces_noalloc(big, big, 40.0)
