@@ -435,6 +435,30 @@ def run_served(args, rank=0, world=1):
     def pct(p):
         return lat[min(len(lat) - 1, int(round(p / 100 * (len(lat) - 1))))]
 
+    # the same kind of runs one at a time with the plain single-box kernels:
+    # the first `served_alone` requests of this rank, each to completion in
+    # its own context on one stream (states of the same recipe)
+    import torch
+    import paper_1911_04712_gb300.dpd as dpd
+    from paper_1911_04712_gb300.workloads import uniform_box_state
+    stream = torch.cuda.current_stream()
+    alone_work, alone_s = 0.0, 0.0
+    for r in reqs[:args.served_alone]:
+        x, v = uniform_box_state(r.L, rho=r.rho, kT=r.kT, seed=r.seed)
+        b = dpd.Box(r.L, a=r.a, gamma=r.gamma, kT=r.kT, rc=1.0, dt=r.dt, seed=r.seed,
+                    stream=stream, stencil=1 if args.stencil == "half" else 0)
+        b.set_state(x, v)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(r.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        alone_s += e0.elapsed_time(e1) / 1000.0
+        alone_work += float(len(x)) * r.steps
+        b.close()
+    alone_rate = alone_work / alone_s if alone_s > 0 else None
+
     return {"workload": f"first {args.requests} requests of the stream: Poisson {args.rate:g}/s, "
                         "L~lognormal(median 16, sigma 0.5) in [8,48], rho in {3,5}, "
                         "a~U[10,80], gamma~U[2,8], kT~U[0.5,2], steps~U{1000..20000}",
@@ -444,7 +468,12 @@ def run_served(args, rank=0, world=1):
             "wall_s": wall, "gpu_busy_s": st["busy_seconds"],
             "policy": "first come first served, admission at 100-step chunk boundaries",
             "stencil": args.stencil,
-            "kT_mean_rel_err_median": statistics.median(kt_err)}
+            "kT_mean_rel_err_median": statistics.median(kt_err),
+            "one_request_at_a_time": {
+                "value": alone_rate, "requests": min(args.served_alone, len(reqs)),
+                "what": "the first requests' boxes, each run alone to its step count with the "
+                        "plain single-box kernels (no sampling)"},
+            "speedup_vs_one_at_a_time": (work / span / alone_rate) if alone_rate else None}
 
 
 def run_native(args):
@@ -687,6 +716,8 @@ def main():
     ap.add_argument("--mix-steps", type=int, default=200)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--served-alone", type=int, default=16,
+                    help="requests of the served stream also run one at a time")
     ap.add_argument("--nbox", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--no-e2e", action="store_true")

@@ -64,7 +64,7 @@ extern "C" {
 #define DPD_ERR_NOMEM (-2)    /* device or host allocation failed / budget exceeded */
 #define DPD_ERR_CUDA (-3)     /* a CUDA runtime call failed                         */
 #define DPD_ERR_STATE (-4)    /* call out of order (e.g. step before set_state)     */
-#define DPD_ERR_NUMERIC (-5)  /* device flagged a non-finite position or force      */
+#define DPD_ERR_NUMERIC (-5)  /* device flagged a non-finite position or force, a runaway particle, or (brick kernel) a cell row whose stencil exceeds its staging */
 #define DPD_ERR_TIMEOUT (-6)  /* a bounded wait expired                              */
 #define DPD_ERR_BUSY (-7)     /* resource in use (e.g. result not ready)            */
 #define DPD_ERR_INTERNAL (-8) /* checked build only: a kernel's index check failed  */
@@ -247,7 +247,10 @@ DPD_API int dpd_debug_rng(const uint32_t *lo, const uint32_t *hi, int64_t n, uin
  * block, pair-list entries per thread and how a warp drains its lists:
  * variants 0-6 per lane, 7-9 balanced over the warp in list order, 10-12
  * spread over the warp with atomic sums (half stencil only; with the full
- * stencil 10-12 drain per lane).  Process-wide tables map density bands
+ * stencil 10-12 drain per lane), 13 the brick kernel that stages cell rows
+ * and their neighbours in shared memory (half stencil; with the full
+ * stencil, and for boxes dense enough to fill half its staging with one
+ * row's stencil, it runs variant 0).  Process-wide tables map density bands
  * (upper bounds of rho = N/V, increasing; the last band also takes every
  * higher density) to a variant.  There are four: table = stencil
  * (DPD_STENCIL_FULL/HALF) for a single box, stencil + DPD_TUNING_PACKED

@@ -221,7 +221,13 @@ int Engine::build_bands() {
     const BoxDev &B = boxes_[b];
     const double rho = (double)B.np / ((double)B.L[0] * B.L[1] * B.L[2]);
     const int table = cfg_.stencil + (nb > 1 ? 2 : 0);  // packed sets have their own table
-    const int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(table, rho);
+    int v = variant_override_ >= 0 ? variant_override_ : tuned_variant(table, rho);
+    // the brick kernel stages one cell row's stencil (6 rows x 5 slices) at
+    // the least: a box whose mean density fills half the staging capacity
+    // that way runs the default direct kernel instead
+    if (v == kBrickVariant && 30.0 * B.np / ((double)B.n[0] * B.n[1] * B.n[2]) >
+                                  0.5 * kBrickCaps)
+      v = 0;
     const int g = B.noise != 0 || B.nspec > 1;  // general kernel
     if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g) {
       runs.back().slot1 = pbase_[b + 1];
@@ -381,7 +387,7 @@ static void brick_shape(const BoxDev &B, int caps, int *by_out, int *bz_out, int
 
 int Engine::build_bricks() {
   const int nb = nbox();
-  const int caps = 896;
+  const int caps = kBrickCaps;
   bricks_h_.clear();
   brick_beg_.assign(nb + 1, 0);
   for (int b = 0; b < nb; ++b) {

@@ -50,6 +50,7 @@ constexpr int kBrickMaxRows = (kBrickMaxBY + 2) * (kBrickMaxBZ + 1);
 constexpr int kBrickWMax = 32;
 constexpr int kBrickListCap = 24;
 constexpr int kBrickMaxCaps = 1024;  // staged particles per block, at most
+constexpr int kBrickCaps = 896;      // staged particles per block used
 constexpr int kBrickVariant = 13;    // the force variant that selects it
 struct BrickGrid {
   const int4 *items;  // device, ordered by box
