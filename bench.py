@@ -103,11 +103,13 @@ STAGE_BYTES = {
 }
 
 
-# DRAM traffic of the force kernel per launch from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/force_direct_L128_rho3.md),
-# valid only while the kernel sources and the tuning table (which picks the
-# variant) hash to the value recorded with it.
-TRAFFIC = {("half", 128.0, 3.0): (401.099e6, "616b2185d99906b0")}
+# DRAM traffic of the force kernel per launch and its L1 data-pipe
+# throughput from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum; l1tex__data_pipe_lsu_wavefronts as a fraction of
+# peak; profiles/force_direct_L128_rho3.md), valid only while the kernel
+# sources and the tuning table (which picks the variant) hash to the value
+# recorded with them.
+TRAFFIC = {("half", 128.0, 3.0): (401.099e6, 0.854, "616b2185d99906b0")}
 KERNEL_SOURCES = ("paper_1911_04712_gb300/csrc/force.cu", "paper_1911_04712_gb300/csrc/dpd_device.cuh",
                   "paper_1911_04712_gb300/csrc/kernels.h", "paper_1911_04712_gb300/tuning_gb300.json")
 
@@ -557,9 +559,10 @@ def run_native(args):
     force_ms = stage_ms[4]
     force_s = force_ms / 1000.0
     traffic = None
+    l1_frac = None
     rec = TRAFFIC.get((args.stencil, float(L), float(rho)))
-    if rec and rec[1] == kernel_hash() and args.philox_rounds == 10:
-        traffic = rec[0]
+    if rec and rec[2] == kernel_hash() and args.philox_rounds == 10:
+        traffic, l1_frac = rec[0], rec[1]
     fma_rate, phx_rate = rates["fma_lane_ops_per_s"], rates["philox_words_per_s"]
     work = force_fma_equiv_per_particle(rho, fma_rate, phx_rate) * n
     achieved = work / force_s / 1e12
@@ -658,6 +661,7 @@ def run_native(args):
             "roofline": {"bound": "alu", "kernel": "force", "achieved": achieved,
                          "peak": peak, "unit": "T FMA-equivalent lane-ops/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "l1_pipe_frac": l1_frac,
                          "peak_from": "measured on this GPU by dpd_issue_rates: FP32 FMA "
                                       f"{fma_rate / 1e12:.2f} T lane-ops/s, Philox-4x32-10 "
                                       f"{phx_rate / 1e12:.4f} T words/s (1 word = "
