@@ -177,6 +177,7 @@ static void worker_main(dpd_queue *q) {
     std::vector<int> src;
     std::vector<Resident> next;
     std::vector<char> fresh;
+    std::vector<char> done_before;  // finished or cancelled before this chunk
     {
       std::unique_lock<std::mutex> lk(q->mu);
       q->cv.wait_for(lk, std::chrono::milliseconds(20),
@@ -186,12 +187,52 @@ static void worker_main(dpd_queue *q) {
         fail_all_locked(q, q->error);
         continue;
       }
-      // boundary: keep running boxes, drop finished or cancelled ones
-      for (size_t k = 0; k < q->resident.size(); ++k) {
-        if (q->state[q->resident[k].ticket] == 2) continue;
-        next.push_back(q->resident[k]);
-        src.push_back((int)k);
-        fresh.push_back(0);
+      // boundary.  Finished (or cancelled) runs stay in the packed set,
+      // frozen, until a re-layout pays: when nothing runs any more, when
+      // they hold an eighth of the set's particles, or when waiting runs
+      // could be admitted (at once, or by dropping finished runs that hold
+      // a thirty-second of the set).  A re-layout drops them and admits
+      // waiting runs; otherwise the set and its captured graphs are kept.
+      int64_t all_n = 0, dead_n = 0, slots_all = 0, cells_all = 0;
+      size_t dead_b = 0;
+      for (const auto &r : q->resident) {
+        all_n += r.n;
+        slots_all += r.n;
+        cells_all += request_cells(r.bp);
+        if (q->state[r.ticket] == 2) {
+          dead_n += r.n;
+          ++dead_b;
+        }
+      }
+      bool relayout = dead_b == q->resident.size() || dead_n * 8 >= all_n;
+      if (!relayout && !q->pending.empty()) {
+        auto it = q->pending.begin();
+        if (q->opts.policy == 1)
+          it = std::min_element(q->pending.begin(), q->pending.end(),
+                                [](const Pending &a, const Pending &b) {
+                                  return (double)a.n * a.steps < (double)b.n * b.steps;
+                                });
+        const bool fits = q->in_use + it->bytes <= q->budget &&
+                          (int64_t)q->resident.size() < q->opts.max_boxes &&
+                          slots_all + it->n <= dpd::kMaxSlots &&
+                          cells_all + request_cells(it->bp) <= dpd::kMaxCellEntries;
+        relayout = fits || (dead_b > 0 && dead_n * 32 >= all_n);
+      }
+      if (!relayout) {
+        for (size_t k = 0; k < q->resident.size(); ++k) {
+          next.push_back(q->resident[k]);
+          src.push_back((int)k);
+          fresh.push_back(0);
+          done_before.push_back(q->state[q->resident[k].ticket] == 2 ? 1 : 0);
+        }
+      } else {
+        for (size_t k = 0; k < q->resident.size(); ++k) {
+          if (q->state[q->resident[k].ticket] == 2) continue;
+          next.push_back(q->resident[k]);
+          src.push_back((int)k);
+          fresh.push_back(0);
+          done_before.push_back(0);
+        }
       }
       // admit waiting requests while the ledger, the box limit and the packed
       // set's slot and cell capacity allow
@@ -200,7 +241,7 @@ static void worker_main(dpd_queue *q) {
         slots += r.n;
         cells += request_cells(r.bp);
       }
-      while (!q->pending.empty() && (int64_t)next.size() < q->opts.max_boxes) {
+      while (relayout && !q->pending.empty() && (int64_t)next.size() < q->opts.max_boxes) {
         auto it = q->pending.begin();
         if (q->opts.policy == 1)
           it = std::min_element(q->pending.begin(), q->pending.end(),
@@ -220,9 +261,12 @@ static void worker_main(dpd_queue *q) {
         q->pending.erase(it);
         src.push_back(-1);
         fresh.push_back(1);
+        done_before.push_back(0);
       }
+      bool live = false;
+      for (size_t k = 0; k < next.size(); ++k) live = live || !done_before[k];
       q->resident = next;
-      if (next.empty()) continue;
+      if (next.empty() || !live) continue;
     }
     int rc = DPD_OK;
     if (q->eng.nbox() != (int)next.size() || !identity(src)) {
@@ -249,11 +293,15 @@ static void worker_main(dpd_queue *q) {
       }
       if (rc == DPD_OK) rc = q->eng.rebuild();
     }
-    // one chunk, ending no later than the earliest finish
+    // cancelled runs still in the set stop moving
+    for (int k = 0; rc == DPD_OK && k < q->eng.nbox(); ++k)
+      if (done_before[k] && q->eng.box_state(k).remaining > 0) rc = q->eng.set_remaining(k, 0);
+    // one chunk, ending no later than the earliest finish of a running box
     int64_t chunk = q->opts.chunk_steps;
     long double ps = 0.0;
     for (int k = 0; k < q->eng.nbox(); ++k)
-      chunk = std::min<int64_t>(chunk, std::max<int64_t>(q->eng.box_state(k).remaining, 1));
+      if (q->eng.box_state(k).remaining > 0)
+        chunk = std::min<int64_t>(chunk, q->eng.box_state(k).remaining);
     for (int k = 0; k < q->eng.nbox(); ++k)
       ps += (long double)q->eng.box_n(k) *
             (long double)std::min<int64_t>(chunk, q->eng.box_state(k).remaining);
@@ -266,7 +314,7 @@ static void worker_main(dpd_queue *q) {
     std::vector<std::pair<int, std::vector<double>>> outs;
     std::vector<std::pair<uint64_t, std::vector<float>>> fin;
     for (int k = 0; rc == DPD_OK && k < q->eng.nbox(); ++k) {
-      if (q->eng.box_state(k).remaining <= 0) {
+      if (!done_before[k] && q->eng.box_state(k).remaining <= 0) {
         std::vector<double> acc(fields);
         rc = q->eng.read_acc(k, acc.data());
         outs.emplace_back(k, std::move(acc));
