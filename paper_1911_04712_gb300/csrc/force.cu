@@ -110,7 +110,11 @@ __device__ __forceinline__ void force_direct(const Packed &P, const BoxDev &B, c
                                              bool real = false) {
   static_assert(!SPREAD || (HALF && !BAL), "the spread drain serves the half stencil");
   static_assert(CAP >= 4, "list too short");
-  constexpr int FLUSH = CAP / 2;
+  // lists are drained after a row once a lane holds more than FLUSH
+  // entries: a quarter of the list for the spread drain (draining a row's
+  // entries together keeps the neighbours each round gathers in few cache
+  // lines), half for the per-lane drains (whose lanes idle on short lists)
+  constexpr int FLUSH = SPREAD ? CAP / 4 : CAP / 2;
   constexpr int U = kScanUnroll;
   constexpr int LS = BAL ? 1 : NT;  // list stride: own row of the warp scratch, or a column
   float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
