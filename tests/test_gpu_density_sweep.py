@@ -13,6 +13,8 @@ force -f for y <= L/2 and +f above, f = 0.05, 2000 steps.
   (the start-up of the flow); the kinetic temperature stays at kT.
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -75,16 +77,26 @@ def test_startup_profile_matches_oracle_statistically(dpd):
         assert prof[: nb // 2].mean() < -0.1 and prof[nb // 2:].mean() > 0.1
 
 
-def test_full_size_profile_matches_oracle_rho3(dpd):
-    """L = 48, rho = 3, a = 25 (331,776 particles), 2000 steps: the GPU and
+SLOW = os.environ.get("DPD_SLOW_TESTS") == "1"
+
+
+@pytest.mark.parametrize("rho,a", [
+    (3, 25.0),
+    pytest.param(5, 15.0, marks=pytest.mark.skipif(not SLOW, reason="oracle ~8 min; DPD_SLOW_TESTS=1")),
+    pytest.param(10, 7.5, marks=pytest.mark.skipif(not SLOW, reason="oracle ~30 min; DPD_SLOW_TESTS=1")),
+])
+def test_full_size_profile_matches_oracle(dpd, rho, a):
+    """L = 48 at rho = 3, a = 25 (331,776 particles), 2000 steps: the GPU and
     the FP64 oracle (cell-list mode, OpenMP) from the same state; the 48-slab
     profiles averaged over the second 1000 steps (50 samples) agree within
-    5 sqrt(2) standard errors, and both show the plug flow -/+ f t."""
+    5 sqrt(2) standard errors, and both show the plug flow -/+ f t.  The
+    rho = 5 and 10 cases (a = 15 and 7.5) run only with DPD_SLOW_TESTS=1:
+    the oracle needs about 8 and 30 minutes for them on 16 host cores."""
     L, nb = 48.0, 48
-    x, v = uniform_box_state(L, rho=3, seed=5)
-    box = _box(dpd, L, 25.0, 5)
+    x, v = uniform_box_state(L, rho=rho, seed=5)
+    box = _box(dpd, L, a, 5)
     box.set_state(x, v)
-    p = O.Params(L=(L, L, L), a=25.0, gamma=4.5, kT=1.0, dt=0.005, seed=5, fb=F0,
+    p = O.Params(L=(L, L, L), a=a, gamma=4.5, kT=1.0, dt=0.005, seed=5, fb=F0,
                  fb_mode=O.FB_POISEUILLE, fb_flow=0, fb_grad=1)
     st = O.State(p, x, v, mode=O.MODE_CELLS)
     box.step(1000)
