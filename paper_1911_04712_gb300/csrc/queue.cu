@@ -191,7 +191,7 @@ static void worker_main(dpd_queue *q) {
       // frozen, until a re-layout pays: when nothing runs any more, when
       // they hold an eighth of the set's particles, or when waiting runs
       // could be admitted (at once, or by dropping finished runs that hold
-      // a thirty-second of the set).  A re-layout drops them and admits
+      // a thirty-second of the set or free a slot under the box limit).  A re-layout drops them and admits
       // waiting runs; otherwise the set and its captured graphs are kept.
       int64_t all_n = 0, dead_n = 0, slots_all = 0, cells_all = 0;
       size_t dead_b = 0;
@@ -216,7 +216,9 @@ static void worker_main(dpd_queue *q) {
                           (int64_t)q->resident.size() < q->opts.max_boxes &&
                           slots_all + it->n <= dpd::kMaxSlots &&
                           cells_all + request_cells(it->bp) <= dpd::kMaxCellEntries;
-        relayout = fits || (dead_b > 0 && dead_n * 32 >= all_n);
+        // a full box limit is freed by dropping any finished run
+        relayout = fits || (dead_b > 0 && (dead_n * 32 >= all_n ||
+                                           (int64_t)q->resident.size() >= q->opts.max_boxes));
       }
       if (!relayout) {
         for (size_t k = 0; k < q->resident.size(); ++k) {
