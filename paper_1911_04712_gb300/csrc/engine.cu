@@ -232,10 +232,13 @@ int Engine::build_bands() {
     if (!runs.empty() && runs.back().variant == v && runs.back().gauss == g) {
       runs.back().slot1 = pbase_[b + 1];
       runs.back().item1 = brick_beg_[b + 1];
+      runs.back().box1 = b + 1;
     } else {
       ForceBand fb{pbase_[b], pbase_[b + 1], v, g};
       fb.item0 = brick_beg_[b];
       fb.item1 = brick_beg_[b + 1];
+      fb.box0 = b;
+      fb.box1 = b + 1;
       runs.push_back(fb);
     }
   }
@@ -252,6 +255,8 @@ int Engine::build_bands() {
     runs.assign(1, ForceBand{0, ntot_, best, anyg});
     runs[0].item0 = 0;
     runs[0].item1 = (int)bricks_h_.size();
+    runs[0].box0 = 0;
+    runs[0].box1 = nb;
   }
   // Packed sets: the warps of each band whose slots span two boxes (the
   // device tests the same: the box of the first and of the last slot, the
@@ -278,6 +283,7 @@ int Engine::build_bands() {
     DPD_CUDA_TRY(cudaMemcpyAsync(d_mixed_, mixed.data(), mixed.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, stream_));
   cfg_.mixed_warps = d_mixed_;
+  cfg_.hboxes = boxes_.data();
   cfg_.nbands = (int)runs.size();
   for (int k = 0; k < cfg_.nbands; ++k) cfg_.band[k] = runs[k];
   return DPD_OK;

@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(kBinThreads) k_integrate_bin(Packed P, bool mo
   const BoxDev B = box_of<SINGLE>(P, b);
   const bool mv = move && P.st[b].remaining > 0;
   const float4 f = mv ? P.frc[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  integrate_one(P, B, p, P.pos[p], P.vel[p], f.x, f.y, f.z, mv, P.st[b].pending != 0);
+  // a stopped box (a step with nothing left to take) keeps its slots and forces
+  integrate_one(P, B, p, P.pos[p], P.vel[p], f.x, f.y, f.z, mv, P.st[b].pending != 0,
+                move && !mv);
 }
 
 // ------------------------------------------------------------------ scan
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_keys(Packed P) {
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
   if (p >= P.ntot) return;
   const int c = P.cellOf[p];
+  if (c < 0) return;  // keeps its slot (stopped box): every particle of its cell does
   if (!DPD_IN_BOUNDS(c >= 0 && c < P.ncell, P.err)) return;
   const int k = P.start[c] + P.slotIn[p];
   if (!DPD_IN_BOUNDS(k >= 0 && k < P.ntot, P.err)) return;
@@ -203,25 +206,33 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_keys(Packed P) {
 // the cell's particles (listed by k_bin_keys), so the order, and with it the
 // full stencil's sums, are reproducible.  Otherwise (half stencil, whose sums
 // are atomic anyway) it is its arrival rank from the count, as in Sec. 3.2.
+// A particle of a stopped box keeps its slot, and its force (which the half
+// stencil's reorder otherwise clears for the atomic sums): it did not move,
+// so its cell's slot range is the one it was placed in.
 template <bool STABLE>
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(Packed P, bool zero_frc) {
   const int p = blockIdx.x * kBinThreads + threadIdx.x;
   if (p >= P.ntot) return;
-  const int c = P.cellOf[p];
+  const int ce = P.cellOf[p];
+  const bool keep = ce < 0;
+  const int c = ce & ~kKeepSlot;
   if (!DPD_IN_BOUNDS(c >= 0 && c < P.ncell, P.err)) return;
   const int s0 = P.start[c];
-  int rank = P.slotIn[p];
-  if constexpr (STABLE) {
-    const int s1 = P.start[c + 1];
-    if (!DPD_IN_BOUNDS(s0 >= 0 && s0 <= s1 && s1 <= P.ntot, P.err)) return;
-    rank = 0;
-    for (int t = s0; t < s1; ++t) rank += (P.keyTmp[t] < p) ? 1 : 0;
+  int dst = p;
+  if (!keep) {
+    int rank = P.slotIn[p];
+    if constexpr (STABLE) {
+      const int s1 = P.start[c + 1];
+      if (!DPD_IN_BOUNDS(s0 >= 0 && s0 <= s1 && s1 <= P.ntot, P.err)) return;
+      rank = 0;
+      for (int t = s0; t < s1; ++t) rank += (P.keyTmp[t] < p) ? 1 : 0;
+    }
+    dst = s0 + rank;
   }
-  const int dst = s0 + rank;
   if (!DPD_IN_BOUNDS(dst >= s0 && dst < P.start[c + 1] && dst < P.ntot, P.err)) return;
   P.pos[dst] = P.pos2[p];
   P.vel[dst] = P.vel2[p];
-  if (zero_frc) P.frc[dst] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (zero_frc && !keep) P.frc[dst] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ------------------------------------------------------------------ stats

@@ -71,7 +71,45 @@ struct ForceBand {
   // and a second launch runs them with the per-lane drain
   int mw_off, mw_count;
   int item0, item1;  // the band's brick work items (brick variant)
+  int box0, box1;    // the band's boxes (whole boxes, slots slot0 .. slot1)
 };
+
+// Box-grouped launches (group.cu), packed sets with the half stencil:
+// every block takes slots of one box only, and the constants of up to
+// kGroupBoxes boxes travel in the kernel parameters, so each block reads
+// its box's constants as block-uniform values, as the single-box kernels
+// read theirs.  BoxHot holds the constants the half stencil's direct force
+// routine reads for uniform noise and one species.
+struct BoxHot {
+  float L[3];
+  float invh[3];
+  int n[3];
+  float xwin;
+  int cellBase, pbase, np;
+  float a, gamma, sig, rc2, inv_rc, kexp;
+  float fb, fb_half;
+  int fb_mode, fb_flow, fb_grad;
+  uint32_t seed_lo, seed_hi;
+};
+constexpr int kGroupBoxes = 240;
+struct BoxGroup {
+  int nbox;                  // boxes in this launch
+  int blk[kGroupBoxes + 1];  // first block of each box; blk[nbox] = blocks launched
+  int box[kGroupBoxes];      // each box's index in the packed set
+  BoxHot hot[kGroupBoxes];
+};
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(BoxGroup) + sizeof(Packed) + 64 <= 32764, "grouped launch parameters");
+BoxHot box_hot(const BoxDev &B);
+// Whether the grouped launch serves this band's kernel: the half stencil's
+// spread-drain variants (10-12) for uniform noise and one species.
+inline bool grouped_variant(int v, bool general, bool half) {
+  return half && !general && v >= 10 && v <= 12;
+}
+// The force stage of boxes [box0, box1) of a packed set (host copies of the
+// box constants in hboxes), in launches of at most kGroupBoxes boxes.
+cudaError_t launch_force_group(const Packed &P, const BoxDev *hboxes, int box0, int box1,
+                               int variant, cudaStream_t s);
 constexpr int kMaxBands = 8;
 constexpr int kNumForceVariants = 14;
 
@@ -84,6 +122,8 @@ struct StepConfig {
   ForceBand band[kMaxBands]{};
   const int *mixed_warps = nullptr;  // device: first slots of the bands' two-box warps
   BrickGrid bricks{};                // work items of the brick force kernel
+  const BoxDev *hboxes = nullptr;    // host copies of the box constants (grouped launches)
+  bool grouped = true;               // packed half stencil: box-grouped launches
 };
 // Whether the variant drains over the whole warp (balanced or spread): such
 // kernels evaluate other lanes' entries with their own box's parameters.
@@ -113,16 +153,24 @@ __device__ __forceinline__ float refold(float x, float L) {
   return (x >= 0.0f && x < L) ? x : 0.0f;
 }
 
+// Cell entries of particles that keep their slot through the reorder
+// (bit 31 of cellOf): the particles of a stopped box, which did not move,
+// so that their slots, and with them the forces held there, stay as they
+// are (the half stencil's reorder otherwise clears the forces).
+constexpr int kKeepSlot = (int)0x80000000u;
+
 // Row a1 for the particle in slot p (Sec. 3.1 item 5, Eq. 1; Sec. 3.2): if
 // `move`, the second half kick of the previous step (when `pending`), this
 // step's first half kick with the force (fx, fy, fz), the drift and the
 // periodic wrap; then the cell of the position, its arrival rank by an
-// atomic count, and the copies the reorder reads.  The integrate kernel and
+// atomic count, and the copies the reorder reads.  `keep`: the particle's
+// box is stopped and the particle keeps its slot.  The integrate kernel and
 // the full stencil's fused force epilogue both call it, so they give the
 // same bits.
-__device__ __forceinline__ void integrate_one(const Packed &P, const BoxDev &B, int p, float4 x,
+template <typename BX>
+__device__ __forceinline__ void integrate_one(const Packed &P, const BX &B, int p, float4 x,
                                               float4 v, float fx, float fy, float fz, bool move,
-                                              bool pending) {
+                                              bool pending, bool keep = false) {
   if (move) {
     const float h = B.hdt_m;
     if (pending) {  // second half kick of the previous step
@@ -160,7 +208,7 @@ __device__ __forceinline__ void integrate_one(const Packed &P, const BoxDev &B, 
   P.pos2[p] = x;
   P.vel2[p] = v;
   if (!DPD_IN_BOUNDS(c >= 0 && c < P.ncell, P.err)) return;
-  P.cellOf[p] = c;
+  P.cellOf[p] = keep ? (c | kKeepSlot) : c;
   P.slotIn[p] = atomicAdd(P.count + c, 1);
 }
 

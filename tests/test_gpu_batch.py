@@ -218,21 +218,34 @@ def test_batch_boxes_match_oracle(mods):
         assert np.abs(d).max() < 1e-3
 
 
-def test_batch_step_limits_freeze_boxes(mods):
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_batch_step_limits_freeze_boxes(mods, stencil):
+    """A box that reached its step limit stays as it stopped while the others
+    go on: its positions, full-step velocities (which take the half kick of
+    its last force) and forces as alone after the same steps (bitwise for
+    the full stencil, up to summation order for the half stencil, whose
+    reorder keeps a stopped box's slots and forces)."""
     D, B = mods
     x1, v1 = uniform_box_state(4.0, rho=3, seed=1)
     x2, v2 = uniform_box_state(5.0, rho=4, seed=2)
     descs = [B.make_desc(4.0, len(x1), seed=1, steps=10), B.make_desc(5.0, len(x2), seed=2)]
-    bt = B.Batch(descs)
+    bt = B.Batch(descs, stencil=stencil)
     bt.set_state(0, x1, v1)
     bt.set_state(1, x2, v2)
     bt.step(25)
     st = bt.stats()
     assert st[0]["step"] == 10 and st[1]["step"] == 25
-    (xa, va), _ = _alone(D, type("S", (), dict(L=4.0, a=25.0, gamma=4.5, kT=1.0, dt=0.005,
-                                               seed=1))(), x1, v1, 10)
+    (xa, va), fa = _alone(D, type("S", (), dict(L=4.0, a=25.0, gamma=4.5, kT=1.0, dt=0.005,
+                                                seed=1))(), x1, v1, 10, stencil)
     xb, vb = bt.get_state(0)
-    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    fb = bt.get_forces(0)
+    if stencil == 0:
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+    else:
+        rms = np.sqrt((fa.astype(np.float64) ** 2).sum(1).mean())
+        assert np.abs(xb.astype(np.float64) - xa).max() < 1e-5
+        assert np.abs(vb.astype(np.float64) - va).max() < 1e-4
+        assert np.abs(fb.astype(np.float64) - fa).max() < 1e-4 * rms
 
 
 def test_batch_rejects_bad_descs_and_unloaded_boxes(mods):
@@ -302,3 +315,56 @@ def test_full_mix_in_the_benchmark_configuration(mods):
         d -= s.L * np.round(d / s.L)
         assert np.abs(d).max() < 1e-3, k
     bt.close()
+
+
+@pytest.mark.parametrize("variant", [10, 11, 12])
+def test_grouped_launches_over_many_boxes(mods, variant):
+    """Half stencil, the packed spread-drain variants: the force stage runs as
+    box-grouped launches (no block spans two boxes; at most 240 boxes per
+    launch, their constants in the launch parameters).  250 small boxes,
+    most with fewer particles than one block, some with the periodic
+    Poiseuille force, some stopped after one step: the first and last boxes,
+    those on both sides of the launch boundary and the stopped ones as each
+    box alone."""
+    D, B = mods
+    rng = np.random.default_rng(11)
+    n = 250
+    Ls = rng.choice([3.0, 3.5, 4.0, 4.5], n)
+    rhos = rng.choice([3.0, 4.0], n)
+    fb = [0.05 if k % 5 == 2 else 0.0 for k in range(n)]
+    limits = [1 if k % 7 == 3 else 0 for k in range(n)]
+    states = [uniform_box_state(L, rho=r, seed=300 + k) for k, (L, r) in enumerate(zip(Ls, rhos))]
+    descs = [B.make_desc(L, len(st[0]), seed=300 + k, steps=lim, body_force=f, body_mode=2,
+                         flow_axis=0, grad_axis=1)
+             for k, (L, st, lim, f) in enumerate(zip(Ls, states, limits, fb))]
+    table = 1 + B.TUNING_PACKED
+    up0, var0 = B.tuning_get(table)
+    nst = 3
+    try:
+        B.tuning_set(table, [1e9], [variant])
+        bt = B.Batch(descs, stencil=1)
+        for k, (x, v) in enumerate(states):
+            bt.set_state(k, x, v)
+        bt.step(nst)
+        st = bt.stats()
+        check = sorted({0, 1, 238, 239, 240, 241, n - 1} | {k for k in range(n) if limits[k]})
+        for k in check:
+            x, v = states[k]
+            box = D.Box(Ls[k], seed=300 + k, stencil=1, poiseuille_f=fb[k] if fb[k] else None,
+                        flow_axis=0, grad_axis=1)
+            box.set_state(x, v)
+            steps = limits[k] if limits[k] else nst
+            box.step(steps)
+            (xa, va), fa = box.get_state(), box.get_forces().astype(np.float64)
+            box.close()
+            assert st[k]["step"] == steps, k
+            (xb, vb), fb_ = bt.get_state(k), bt.get_forces(k).astype(np.float64)
+            d = xb.astype(np.float64) - xa
+            d -= Ls[k] * np.round(d / Ls[k])
+            rms = np.sqrt((fa ** 2).sum(1).mean())
+            assert np.abs(d).max() < 1e-5, k
+            assert np.abs(vb.astype(np.float64) - va).max() < 1e-4, k
+            assert np.abs(fb_ - fa).max() < 1e-4 * rms, k
+        bt.close()
+    finally:
+        B.tuning_set(table, up0, var0)
