@@ -323,17 +323,22 @@ def test_grouped_launches_over_many_boxes(mods, variant):
     box-grouped launches (no block spans two boxes; at most 240 boxes per
     launch, their constants in the launch parameters).  250 small boxes,
     most with fewer particles than one block, some with the periodic
-    Poiseuille force, some stopped after one step: the first and last boxes,
-    those on both sides of the launch boundary and the stopped ones as each
-    box alone."""
+    Poiseuille force, some stopped after one step and three empty (one of
+    them beside the launch boundary), all in one density band so that they
+    are packed in the caller's order: the first and last boxes, those on
+    both sides of the launch boundary and the stopped ones as each box
+    alone."""
     D, B = mods
     rng = np.random.default_rng(11)
     n = 250
+    empty = {5, 240, 249}
     Ls = rng.choice([3.0, 3.5, 4.0, 4.5], n)
-    rhos = rng.choice([3.0, 4.0], n)
+    rhos = rng.choice([2.5, 3.0], n)
     fb = [0.05 if k % 5 == 2 else 0.0 for k in range(n)]
     limits = [1 if k % 7 == 3 else 0 for k in range(n)]
-    states = [uniform_box_state(L, rho=r, seed=300 + k) for k, (L, r) in enumerate(zip(Ls, rhos))]
+    states = [(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32)) if k in empty
+              else uniform_box_state(L, rho=r, seed=300 + k)
+              for k, (L, r) in enumerate(zip(Ls, rhos))]
     descs = [B.make_desc(L, len(st[0]), seed=300 + k, steps=lim, body_force=f, body_mode=2,
                          flow_axis=0, grad_axis=1)
              for k, (L, st, lim, f) in enumerate(zip(Ls, states, limits, fb))]
@@ -347,7 +352,10 @@ def test_grouped_launches_over_many_boxes(mods, variant):
             bt.set_state(k, x, v)
         bt.step(nst)
         st = bt.stats()
-        check = sorted({0, 1, 238, 239, 240, 241, n - 1} | {k for k in range(n) if limits[k]})
+        for k in empty:
+            assert st[k]["n"] == 0, k
+        check = sorted(({0, 1, 238, 239, 241, 242, n - 2} | {k for k in range(n) if limits[k]})
+                       - empty)
         for k in check:
             x, v = states[k]
             box = D.Box(Ls[k], seed=300 + k, stencil=1, poiseuille_f=fb[k] if fb[k] else None,
