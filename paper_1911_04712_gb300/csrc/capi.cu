@@ -194,8 +194,11 @@ int dpd_set_state_species(dpd_ctx *ctx, int64_t n, const float *pos, const float
       if (species[i] < 0 || species[i] >= ctx->bp.nspec)
         return dpd::set_error(DPD_ERR_ARG, "particle %lld: species %d outside 0..%d",
                               (long long)i, species[i], ctx->bp.nspec - 1);
+  // a loaded context of the same size keeps its layout (its parameters
+  // reach the engine as they change)
+  const bool same = ctx->loaded && ctx->eng.restart_same_layout({n});
   ctx->loaded = false;
-  int rc = ctx->eng.layout({ctx->bp}, {n});
+  int rc = same ? DPD_OK : ctx->eng.layout({ctx->bp}, {n});
   if (rc) return rc;
   rc = ctx->eng.load_box(0, pos, vel, where == DPD_WHERE_DEVICE, species);
   if (rc) return rc;

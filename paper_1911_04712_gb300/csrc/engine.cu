@@ -579,6 +579,15 @@ int Engine::layout(const std::vector<BoxParams> &params, const std::vector<int64
   return rc2;
 }
 
+bool Engine::restart_same_layout(const std::vector<int64_t> &np) {
+  if (boxes_.empty() || np.size() != boxes_.size() || sample_every_ > 0) return false;
+  for (size_t b = 0; b < np.size(); ++b)
+    if (np[b] != (int64_t)(pbase_[b + 1] - pbase_[b])) return false;
+  st_host_.assign(np.size(), BoxState{0ull, 0ll, 0, 0});
+  from_h_.assign(np.size(), 0ll);
+  return true;
+}
+
 int Engine::update_params(const std::vector<BoxParams> &params) {
   if (params.size() != boxes_.size()) return set_error(DPD_ERR_ARG, "box count changed");
   for (size_t b = 0; b < params.size(); ++b) {

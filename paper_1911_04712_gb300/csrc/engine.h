@@ -107,6 +107,11 @@ class Engine {
   int layout(const std::vector<BoxParams> &params, const std::vector<int64_t> &np);
   // Re-upload descriptors after a parameter change (same layout).
   int update_params(const std::vector<BoxParams> &params);
+  // A new state with the same particle counts and parameters: the packing,
+  // the tables and the captured graphs stay, and the box states are reset
+  // as layout() resets them.  Returns false (nothing changed) when the
+  // counts differ or sampling is on, and layout() is needed.
+  bool restart_same_layout(const std::vector<int64_t> &np);
 
   // Load particles of one box (n x 3 host or device arrays).
   int load_box(int box, const float *pos, const float *vel, bool device_ptr,

@@ -244,6 +244,35 @@ def test_full_stencil_is_bitwise_reproducible_and_graph_equals_direct(dpd):
         assert np.array_equal(xg, outs[0][0]) and np.array_equal(vg, outs[0][1])
 
 
+def test_reloading_a_state_equals_a_fresh_context(dpd):
+    """A context that loads a new state of the same size keeps its packing,
+    tables and captured graphs: its run from the new state is the run of a
+    fresh context, bitwise (full stencil), also after a parameter change
+    between the two runs; a state of another size takes a new layout."""
+    L = 8.0
+    x1, v1 = uniform_box_state(L, rho=3, seed=1)
+    x2, v2 = uniform_box_state(L, rho=3, seed=2)
+    x3, v3 = uniform_box_state(L, rho=4, seed=3)
+    p = _params(L, seed=1)
+    box = _box(dpd, p)
+    box.set_state(x1, v1)
+    box.step(40)                                 # graphs captured
+    box.set_param(dpd.PARAM_BODYFORCE, 0.3)
+    for x, v in ((x2, v2), (x3, v3), (x3, v3)):
+        box.set_state(x, v)
+        box.step(45)
+        ref = _box(dpd, p)
+        ref.set_param(dpd.PARAM_BODYFORCE, 0.3)
+        ref.set_state(x, v)
+        ref.step(45)
+        (xa, va), (xb, vb) = box.get_state(), ref.get_state()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert np.array_equal(box.get_forces(), ref.get_forces())
+        assert box.stats()["step"] == ref.stats()["step"] == 45
+        ref.close()
+    box.close()
+
+
 @pytest.mark.parametrize("body", [False, True])
 def test_fused_integrate_gives_the_same_bits(dpd, body):
     """Full stencil: the force kernel doing the next step's kick, drift and
