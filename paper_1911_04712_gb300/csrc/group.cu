@@ -48,10 +48,11 @@ namespace {
 
 // The kernels are the spread-drain variants: the per-lane and balanced
 // drains, compiled this way, need twice the registers of their packed
-// kernels and stay with those.  Register bound: nine blocks of 128 threads
-// per SM (56 registers, no spills), what the single-box kernels use.
+// kernels and stay with those.  The compiler's 60 registers (eight blocks
+// of 128 threads per SM) ran 5 % faster than a bound of 56 (nine blocks),
+// under which the block-uniform constants are re-read more often.
 template <int NT, int CAP>
-__global__ void __launch_bounds__(NT, 1152 / NT)
+__global__ void __launch_bounds__(NT)
     k_force_group(Packed P, const __grid_constant__ BoxGroup G) {
   __shared__ uint32_t smem_list[CAP * NT];
   __shared__ float4 smem_own[2 * NT];
