@@ -50,12 +50,12 @@ UNIT = "particle-steps/s"
 # instructions (r, w, e . v_ij, the three terms, the update, the noise map)
 # plus one Philox-4x32-10 word.  The roofline weighs the Philox word by the
 # measured issue rates: FMA-equivalent work = FP32 instructions + words x
-# (FMA rate / Philox word rate), against the measured FMA rate.  (Survey
-# count for comparison: 7 slots per candidate and 110 per pair -- 30 FP32 and
-# 80 integer -- against SMs x 128 lanes x clock.)
+# (FMA rate / Philox word rate), against the measured FMA rate.  (An
+# unweighted count for comparison: 7 slots per candidate and 110 per pair --
+# 30 FP32 and 80 integer -- against SMs x 128 lanes x clock.)
 CAND_SLOTS = 7
 PAIR_FP32 = 30
-SURVEY_PAIR_SLOTS = 110
+UNWEIGHTED_PAIR_SLOTS = 110
 
 
 def force_counts(rho: float):
@@ -65,9 +65,9 @@ def force_counts(rho: float):
 
 
 def force_slots_per_particle(rho: float) -> float:
-    """The survey's unweighted count (lane-instruction slots per particle)."""
+    """The unweighted count (lane-instruction slots per particle)."""
     cands, pairs = force_counts(rho)
-    return cands * CAND_SLOTS + pairs * SURVEY_PAIR_SLOTS
+    return cands * CAND_SLOTS + pairs * UNWEIGHTED_PAIR_SLOTS
 
 
 def force_fma_equiv_per_particle(rho: float, fma_rate: float, philox_rate: float) -> float:
@@ -568,7 +568,7 @@ def run_native(args):
     work = force_fma_equiv_per_particle(rho, fma_rate, phx_rate) * n
     achieved = work / force_s / 1e12
     peak = fma_rate / 1e12
-    survey_achieved = force_slots_per_particle(rho) * n / force_s / 1e12
+    unweighted_achieved = force_slots_per_particle(rho) * n / force_s / 1e12
     fp32_achieved = force_flops_per_particle(rho) * n / force_s / 1e12
     fp32_peak = 2.0 * peak
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -668,9 +668,9 @@ def run_native(args):
                                       f"{phx_rate / 1e12:.4f} T words/s (1 word = "
                                       f"{fma_rate / phx_rate:.1f} FMA slots)",
                          "work_per_particle": force_fma_equiv_per_particle(rho, fma_rate, phx_rate),
-                         "survey_count": {"achieved": survey_achieved, "peak": lane_peak,
+                         "unweighted_count": {"achieved": unweighted_achieved, "peak": lane_peak,
                                           "unit": "T lane-ops/s",
-                                          "frac": (survey_achieved / lane_peak) if lane_peak else None,
+                                          "frac": (unweighted_achieved / lane_peak) if lane_peak else None,
                                           "peak_from": f"{sms} SMs x 128 lanes x {sm_mhz} MHz "
                                                        f"({clock_src})"},
                          "fp32": {"achieved": fp32_achieved, "peak": fp32_peak,
